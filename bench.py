@@ -1,0 +1,352 @@
+"""Throughput benchmark of the CSPH-TVD + Exner step on GB300.
+
+Workload: half-wet fractal terrain, 16384 x 16384 cells (268M), dx = 5 m,
+20 m relief with a carved channel, 50 % wet with a 2 m dam-break step so
+fronts move, Manning n per 64 x 64 block, FP32 state with FP64 dt / mass
+bookkeeping; K timed steps.  Metric: Gcell-updates/s, counting every cell of
+the grid each step (HGS-skipped dry blocks included).
+
+One JSON line on rank 0:
+  value       device-timed (CUDA events on the solver's stream), inputs resident
+  e2e         the same through the C ABI with host buffers: H2D of the state,
+              K steps, D2H of the state, all inside the timed region
+  roofline    the fused step kernel against the measured HBM copy bandwidth;
+              algorithmic bytes = 32 B x cells of the computed and copied blocks
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+With --impl reference, the oracle arm alone.  With --gpus N under torchrun,
+N independent replicas (the method is single-GPU): value = all cells / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s per CSPH-TVD+Exner step"
+UNIT = "Gcell/s"
+BYTES_PER_CELL = 32  # FP32 AoS {H, Hu, Hv, b}: 16 B read + 16 B write
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("swe_kernels.cuh", "swe_launch.cuh", "swe_internal.h"):
+        with open(os.path.join(ROOT, "paper_2103_15196_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(n):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to this grid; None if absent or taken on other kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_fp32_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != _kernel_hash():
+            return None
+        per_cell = float(kv["dram_bytes_per_cell"])
+        return per_cell * n * n
+    except Exception:
+        return None
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = str(index)
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            self.index = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            pass
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_workload(n, seed=3):
+    from paper_2103_15196_gb300 import inputs as I
+    return I.half_wet(n, dx=5.0, seed=seed)
+
+
+def cpu_baseline(sc, budget_s=12.0, win=1024):
+    """The FP64 oracle as it stands, on windows of the workload's first state,
+    all host cores: cell-updates/s (dt from the window's own Eq. 7 terms)."""
+    from oracle import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    n = sc.nx
+    w = min(win, n)
+    y0 = x0 = (n - w) // 2
+    sl = (slice(y0, y0 + w), slice(x0, x0 + w))
+    H = np.ascontiguousarray(sc.H[sl], dtype=np.float64)
+    b = np.ascontiguousarray(sc.b[sl], dtype=np.float64)
+    Z = np.zeros_like(H)
+    ncell = np.ascontiguousarray(sc.manning_per_cell()[sl], dtype=np.float64)
+    p = O.Params(nx=w, ny=w, dx=sc.dx, tile_x=64, tile_y=64)
+    st = O.State(H, Z, Z.copy(), b)
+    cells, t0 = 0, time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        st, info = O.step(p, st, ncell)
+        cells += w * w
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": cells / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps (K1-K8, HGS on) of the central {w}x{w} window "
+                      f"of the {n}^2 workload, {el:.1f} s"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: K steps of a central window of
+    the workload, the window sized so the K + W steps take ~ref_seconds."""
+    from oracle import oracle as O
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    n = args.size
+    sc = make_workload(n)
+    cores = O.set_threads(os.cpu_count() or 1)
+
+    def window(w):
+        y0 = (n - w) // 2
+        sl = (slice(y0, y0 + w), slice(y0, y0 + w))
+        H = np.ascontiguousarray(sc.H[sl], dtype=np.float64)
+        Z = np.zeros_like(H)
+        st = O.State(H, Z, Z.copy(), np.ascontiguousarray(sc.b[sl], dtype=np.float64))
+        ncell = np.ascontiguousarray(sc.manning_per_cell()[sl], dtype=np.float64)
+        return O.Params(nx=w, ny=w, dx=sc.dx, tile_x=64, tile_y=64), st, ncell
+
+    p, st, ncell = window(256)
+    t0 = time.perf_counter()
+    O.step(p, st, ncell)
+    per_cell = (time.perf_counter() - t0) / (256 * 256)
+    per_step = args.ref_seconds / max(1, args.steps + args.warmup)
+    w = int(min(min(n, 2048), max(64, (per_step / per_cell) ** 0.5)))
+    p, st, ncell = window(w)
+    for _ in range(args.warmup):
+        st, _ = O.step(p, st, ncell)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        st, _ = O.step(p, st, ncell)
+    el = time.perf_counter() - t0
+    v = float(w) * w * max(1, args.steps) / el / 1e9
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"{args.steps} FP64 oracle steps (K1-K8, HGS on) of the central {w}x{w} window of the "
+                    f"{n}^2 workload, {el:.1f} s"}
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"half-wet fractal terrain {n}x{n}, dx=5 m, Manning per 64^2 block; "
+                                   f"oracle on 1024^2 windows", "grid": n},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2103_15196_gb300 import swe
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    n, K, W = args.size, args.steps, args.warmup
+    sc = make_workload(n)
+    stream = torch.cuda.Stream()
+    S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=0 if args.hgs_off else 1)
+    S.set_manning(sc.manning, block=64)
+    H32 = [np.ascontiguousarray(a, dtype=np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)]
+    S.set_state(*H32)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # --- device-timed region, inputs resident
+    S.run_steps(W)
+    S.sync()
+    d0 = S.diag()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        S.run_steps(K)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    S.sync()
+    d1 = S.diag()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = float(n) * n * K * world
+    value = cells / (ms * 1e-3) / 1e9
+    comp = d1["cells_computed"] - d0["cells_computed"]
+    copied = d1["cells_copied"] - d0["cells_copied"]
+    alg_bytes_launch = BYTES_PER_CELL * (comp + copied) / K
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes_launch / (ms * 1e-3 / K) / 1e9
+    traffic = _profile_traffic(n)
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ke = max(1, min(K, args.e2e_steps))
+        host_in = [torch.from_numpy(a).pin_memory().numpy() for a in H32]
+        host_out = [torch.empty((n, n), dtype=torch.float32).pin_memory().numpy() for _ in range(4)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.set_state(*host_in)
+        S.run_steps(Ke)
+        S.get_state(out=host_out)
+        t1 = time.perf_counter()
+        barrier()
+        el = t1 - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": float(n) * n * Ke * world / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(4 * n * n * 4 / Ke), "d2h_bytes_per_step": int(4 * n * n * 4 / Ke),
+               "steps": Ke, "seconds": el}
+    dd = S.diag()
+    S.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(sc, budget_s=args.cpu_seconds)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"half-wet fractal terrain {n}x{n} ({n * n} cells), dx=5 m, 20 m relief, "
+                               f"carved channel, 2 m dam-break step, Manning per 64^2 block, FP32 state, "
+                               f"FP64 dt/accumulators, HGS {'off' if args.hgs_off else 'on'}",
+                   "grid": n, "l2_flush": "inputs larger than L2 (2 x 4.3 GB ping-pong state)",
+                   "parallelism": f"{world} independent replica(s)",
+                   "block": [dd["tile_x"], dd["tile_y"]]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "step_kernel<float,256>",
+                     "algorithmic_bytes_per_launch": alg_bytes_launch,
+                     "note": "launch duration = timed region / K (includes the one-thread dt kernel)"},
+        "hgs": {"active_cell_fraction": comp / (float(n) * n * K), "copied_cell_fraction": copied / (float(n) * n * K),
+                "all_cell_equiv_GBps": BYTES_PER_CELL * n * n / (ms * 1e-3 / K) / 1e9,
+                "wet_cells_end": dd["wet_cells"], "t_end": dd["t"]},
+        "e2e": e2e,
+        "gpu_launches": 2 * K,
+        "clocks": clocks,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--hgs-off", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * swe.h -- C ABI of the GB300 (sm_103a) CSPH-TVD + Exner solver.
+ *
+ * One time step advances the coupled Saint-Venant + Exner system written as
+ * Eq. 6 of Khrapov & Khoperskov (2020): U = (H, Hu, Hv, b) with the Exner law
+ * of Eq. 1 (porosity psi), the solid discharge of Eq. 2-3 (Grass law with
+ * bed-slope term, A_J constant or from Eq. 4), the Shamov threshold of Eq. 5,
+ * and the time step of the stability bound Eq. 7.  The step runs the paper's
+ * kernels K1 (wet census of each block, the hierarchical grid system), K2-K6
+ * (Lagrangian predictor/corrector) and K7-K8 (Eulerian fluxes and update) of
+ * Sec. 3 as one fused CUDA kernel per step plus a one-thread kernel that forms
+ * dt.  Everything runs on one GPU; state stays resident in device memory.
+ *
+ * Conventions, for every call:
+ *   - Returns a swe_status; nothing is thrown across the ABI.  After a
+ *     non-OK status, swe_last_error(handle) gives a one-line reason.
+ *   - Arrays are row-major [ny][nx], x fastest.  Host arrays are read or
+ *     written synchronously inside the call and stay owned by the caller.
+ *   - The library owns all device memory it allocates (cudaMalloc) and frees
+ *     it in swe_destroy.  Device pointers passed in (the *_device variants)
+ *     stay owned by the caller and are only read/written on the handle's stream.
+ *   - A handle is bound to the CUDA device current at swe_create and to the
+ *     stream given there; calls on one handle must not overlap.
+ *   - Call order: create -> set_manning (optional, default n = 0.03) ->
+ *     set_sources (optional) -> set_state -> step/advance -> get_state.
+ *     Stepping before set_state returns SWE_ESTATE.
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swe_handle swe_handle;
+
+typedef enum {
+    SWE_OK = 0,
+    SWE_EINVAL = 1,   /* invalid argument (sizes, parameters, null pointers) */
+    SWE_ENOMEM = 2,   /* device or host allocation failed */
+    SWE_ECUDA = 3,    /* a CUDA runtime call failed */
+    SWE_ENUMERIC = 4, /* non-finite result, or a depth below -neg_tol */
+    SWE_ETIMEOUT = 5, /* a bounded device wait gave up */
+    SWE_ESTATE = 6    /* call out of order (e.g. step before set_state) */
+} swe_status;
+
+enum { SWE_FP64 = 0, SWE_FP32 = 1 };          /* state/flux precision */
+enum { SWE_HOST = 0, SWE_DEVICE = 1 };        /* where a buffer lives */
+
+/* Model parameters (plain data, copied at swe_create).  swe_params_default
+ * fills the defaults named below. */
+typedef struct {
+    int nx, ny;          /* grid size in cells (>= 1 each) */
+    double dx;           /* cell size h in metres (Eq. 7: h is the cell size) */
+    double g;            /* gravity, 9.81 */
+    double cfl_K;        /* Courant number K of Eq. 7, 0 < K < 1; default 0.4 */
+    double eps_wet;      /* wet threshold Eps of kernel K1; default 1e-4 m */
+    double dt_max;       /* cap on dt when no Eq. 7 term is finite; default 1 s */
+    double psi;          /* porosity of Eq. 1, 0 <= psi < 1; default 0.4 */
+    int sediment_on;     /* Exner coupling on (1) / off (0); default 1 */
+    int aj_mode;         /* 0: constant A_J (Eq. 3); 1: A_J from Eq. 4; default 0 */
+    double A_J;          /* Grass coefficient of Eq. 3; default 0.001 */
+    double m_exp;        /* Grass exponent m of Eq. 3; default 2 */
+    double C_J;          /* bed-slope coefficient of Eq. 2; default 2.0 */
+    double d50;          /* median grain size, Eq. 4-5; default 5e-4 m */
+    double s_rel;        /* relative density rho_s/rho, Eq. 4; default 2.65 */
+    double C_Sh;         /* Shamov coefficient of Eq. 5; default 5.0 */
+    int dt_literal_D;    /* 1: D of Eq. 7 as printed, 0: C_J-scaled D; default 0 */
+    int precision;       /* SWE_FP64 or SWE_FP32; default SWE_FP32 */
+    int hgs_skip;        /* skip dry blocks (K1 rule of Sec. 3); default 1 */
+    int tile_rows;       /* rows per block strip; 0 = chosen by the library */
+    int block_cols;      /* threads (columns) per block, 128 or 256; 0 = auto */
+    double neg_tol;      /* H' < -neg_tol => SWE_ENUMERIC; default 1e-10 (FP64), 1e-4 (FP32) */
+} swe_params;
+
+/* Diagnostics of the current state (swe_get_diag). Volumes are FP64 sums
+ * times h^2 over all cells. */
+typedef struct {
+    double t;               /* simulated time of the current state */
+    double dt_last;         /* dt of the last step taken */
+    double dt_next;         /* dt the next step will take (Eq. 7, before any t_end clip) */
+    int binding;            /* Eq. 7 term that set dt_last: 0 h/(2 vp), 1 h/vs, 2 h^2/(2D), 3 dt_max, 4 t_end */
+    double water_volume;    /* sum H h^2 */
+    double sediment_volume; /* sum b h^2 */
+    double inflow_volume;   /* total volume added by sources since set_state */
+    int64_t steps;          /* steps taken since set_state */
+    int64_t wet_cells;      /* cells with H > eps_wet */
+    int32_t active_tiles;   /* blocks computed in the last step (HGS) */
+    int32_t total_tiles;    /* blocks per step */
+    int32_t tile_x, tile_y; /* HGS block size in cells */
+    uint32_t status;        /* device status bits: 1 non-finite, 2 negative depth */
+    uint64_t cells_computed;/* cells of computed blocks, summed over steps since set_state */
+    uint64_t cells_copied;  /* cells of skipped blocks that were copied, summed likewise */
+} swe_diag;
+
+/* Fills *p with the defaults above for an nx x ny grid of cell size dx. */
+swe_status swe_params_default(swe_params *p, int nx, int ny, double dx);
+
+/* Creates a solver for the grid and model of *p on the current CUDA device,
+ * issuing all work on `cuda_stream` (a cudaStream_t; NULL = default stream).
+ * Allocates two state buffers and small tables in device memory. */
+swe_status swe_create(const swe_params *p, void *cuda_stream, swe_handle **out);
+
+/* Frees all device and host memory of the handle (NULL is accepted). */
+swe_status swe_destroy(swe_handle *h);
+
+/* Manning coefficient n_M(x, y) (Sec. 3, an input field of the Main block),
+ * used by bottom friction and by Eq. 4.  block = 0 or 1: n holds nx*ny
+ * per-cell values; block = B (a power of two): n holds ceil(ny/B) x ceil(nx/B)
+ * values, one per B x B block.  Values must be finite and >= 0. */
+swe_status swe_set_manning(swe_handle *h, const double *n, int block);
+
+/* Water sources sigma of Eq. 6 (row 1): the inflow Q(t) [m^3/s], piecewise
+ * linear through (t[k], Q[k]), k < nk, constant beyond its ends, is spread
+ * evenly over the cells flagged in mask (uint8, nx*ny, nonzero = source; these
+ * are the Index_Q cells of kernel K1).  Water enters with zero momentum.
+ * mask = NULL or nk = 0 removes all sources.  t must be increasing. */
+swe_status swe_set_sources(swe_handle *h, const uint8_t *mask, const double *t,
+                           const double *Q, int nk);
+
+/* Bed source q_b^+ - q_b^- of Eq. 1 per cell (nx*ny values, m/s of bed
+ * material per unit area); NULL removes it.  Default: none. */
+swe_status swe_set_bed_source(swe_handle *h, const double *q);
+
+/* Sets the state (H, Hu, Hv, b) from host FP64 arrays of nx*ny values and
+ * resets t to 0.  Dry cells (H <= eps_wet) are given zero momentum. */
+swe_status swe_set_state(swe_handle *h, const double *H, const double *Hu,
+                         const double *Hv, const double *b);
+
+/* As swe_set_state, with the arrays' type (SWE_FP64 / SWE_FP32) and location
+ * (SWE_HOST / SWE_DEVICE, device pointers on this handle's device) given. */
+swe_status swe_set_state_ex(swe_handle *h, const void *H, const void *Hu, const void *Hv,
+                            const void *b, int dtype, int where);
+
+/* Copies the current state out to host FP64 arrays (any may be NULL). */
+swe_status swe_get_state(swe_handle *h, double *H, double *Hu, double *Hv, double *b);
+
+/* As swe_get_state with the output type and location given. */
+swe_status swe_get_state_ex(swe_handle *h, void *H, void *Hu, void *Hv, void *b,
+                            int dtype, int where);
+
+/* One time step with dt from Eq. 7; *dt_taken (nullable) receives it.
+ * Synchronises the stream and checks the device status word. */
+swe_status swe_step(swe_handle *h, double *dt_taken);
+
+/* Steps until t reaches t_end; the last dt is clipped so t lands exactly on
+ * t_end.  Runs captured CUDA graphs of several steps and polls a device flag
+ * once per graph replay.  *steps_taken (nullable) receives the step count. */
+swe_status swe_advance(swe_handle *h, double t_end, int64_t *steps_taken);
+
+/* Exactly nsteps steps (dt from Eq. 7, no t_end) queued on the stream without
+ * host synchronisation; the status word is checked by swe_sync / swe_get_diag. */
+swe_status swe_run_steps(swe_handle *h, int64_t nsteps);
+
+/* Waits for the handle's stream and checks the device status word. */
+swe_status swe_sync(swe_handle *h);
+
+/* Current time, and setting it (the hydrograph is evaluated at absolute t). */
+swe_status swe_get_time(swe_handle *h, double *t);
+swe_status swe_set_time(swe_handle *h, double t);
+
+/* Diagnostics of the current state (runs an FP64 reduction over the grid). */
+swe_status swe_get_diag(swe_handle *h, swe_diag *out);
+
+/* Index_block of kernel K1 for the current state: wet-or-source cell count of
+ * each HGS block, row-major [tiles_y][tiles_x]; out may be NULL to query the
+ * block grid size only. */
+swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, int *tiles_y);
+
+/* One-line description of the last error on the handle ("" if none). */
+const char *swe_last_error(const swe_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_H */

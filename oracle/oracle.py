@@ -262,7 +262,7 @@ def run(p: Params, st: State, n, nsteps: int, src=None, qb=None, hydro=None, t: 
         if t_end > 0 and t >= t_end:
             break
         st, info = step(p, st, n, src=src, qb=qb, hydro=hydro, t=t, t_end=t_end)
-        t += info.dt
+        t = t_end if info.binding == 4 else t + info.dt   # a clipped step lands on t_end
         infos.append(info)
         if on_step is not None:
             on_step(st, t, info)

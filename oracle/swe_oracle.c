@@ -219,18 +219,18 @@ typedef struct {
 
 #define E(e, i, j) ((long)((j) - (e)->y0) * (e)->W + ((i) - (e)->x0))
 
-/* Pressure + bed-slope force on a particle (Eq. 6 Phi row 2, -g H grad(H+b);
+/* Pressure + bed-slope force per unit mass (Eq. 6 Phi row 2, -g H grad(H+b);
  * READING on the sign: the printed +gH grad(H+b) sits on the right-hand side of
  * dU/dt + ... = Phi, physically the force is -g H grad(H+b)).
- * Face form (READING): per unit area f = -g/(2h) [Hb_E (eta_E - eta) + Hb_W
- * (eta - eta_W)] with the face-mean depth Hb = (H + H_nb)/2, which for a flat
- * bed is the central difference of g H^2/2 (momentum-conservative, so dam-break
- * shocks converge to the right states) and vanishes for a flat free surface.
- * The acceleration is f divided by the particle mass per unit area H^n.
+ * Central form (READING): a = -g/(2h) (eta_E' - eta_W') * Hs/H^n, where Hs is
+ * the particle depth at the stage (H^n for K2, H^{n+1/2} = H^n/A for K5) and
+ * H^n the particle mass per unit area: summed over cells, H^n a telescopes
+ * into face differences of g Hs^2/2 on a flat bed (momentum-conservative,
+ * dam-break shocks converge to the right states), the acceleration stays
+ * bounded by g |d eta| / (2 h A), and a flat free surface feels no force.
  * Wet/dry rule (READING): a dry neighbour whose bed lies at or above the
  * cell's free surface acts as a wall (its level is taken equal to the cell's
- * own level).  Dry cells feel no force.  Hs/eta are the depth and level at the
- * stage (t_n or t_{n+1/2}); Hn is the t_n depth. */
+ * own level).  Dry cells feel no force. */
 static void forces(const orc_params *p, ext_t *e, const double *Hs, const double *eta,
                    int i0, int i1, int j0, int j1, double *fx, double *fy)
 {
@@ -239,16 +239,16 @@ static void forces(const orc_params *p, ext_t *e, const double *Hs, const double
         for (int i = i0; i < i1; ++i) {
             long c = E(e, i, j);
             if (!e->wet[c]) { fx[c] = 0.0; fy[c] = 0.0; continue; }
-            double ec = eta[c], hc = Hs[c];
+            double ec = eta[c];
             long nb[4] = { E(e, i + 1, j), E(e, i - 1, j), E(e, i, j + 1), E(e, i, j - 1) };
-            double en[4], hb[4];
+            double en[4];
             for (int q = 0; q < 4; ++q) {
                 long k = nb[q];
                 en[q] = (!e->wet[k] && e->b[k] >= ec) ? ec : eta[k];
-                hb[q] = 0.5 * (hc + Hs[k]);
             }
-            fx[c] = -(coef * (hb[0] * (en[0] - ec) + hb[1] * (ec - en[1]))) / e->H[c];
-            fy[c] = -(coef * (hb[2] * (en[2] - ec) + hb[3] * (ec - en[3]))) / e->H[c];
+            double r = Hs[c] / e->H[c];
+            fx[c] = -(coef * (en[0] - en[1])) * r;
+            fy[c] = -(coef * (en[2] - en[3])) * r;
         }
 }
 

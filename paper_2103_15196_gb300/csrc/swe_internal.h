@@ -1,0 +1,72 @@
+// Internal declarations shared by the C-ABI host code and the kernel
+// translation units (one per precision).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+// Step bookkeeping that lives in device memory so a whole sequence of steps
+// can be queued (or captured in a CUDA graph) without host round trips.
+// Written by the one-thread `between` kernel, read by the step kernel.
+struct SweDev {
+    double t;             // time of the current state
+    double dt;            // dt of the step scheduled next (0: none)
+    double dt_unclipped;  // Eq. 7 value before the t_end clip
+    double t_end;         // clip target of swe_advance (+inf when stepping freely)
+    double dHs;           // depth added to each source cell by the scheduled step
+    double inflow_total;  // FP64 total inflow volume since set_state
+    double dt_last;       // dt of the last committed step
+    double dtdx, hdt, c4, cb;  // dt/h, dt/2, dt/(4h), dt/(h(1-psi)) of the scheduled step
+    long long n;          // index of the current state: state^n lives in buf[n & 1]
+    int scheduled;        // a step with dt > 0 is prepared
+    int done;             // t reached t_end
+    int binding;          // Eq. 7 term behind dt
+    int binding_last;
+    unsigned status;      // 1: non-finite value, 2: depth below -neg_tol
+    int active_tiles;     // blocks computed by the running step
+    int active_last;      // blocks computed by the last committed step
+    unsigned long long cells_computed;  // cells in blocks computed, summed over steps
+    unsigned long long cells_copied;    // cells in blocks copied (skipped, buffers differed)
+    unsigned long long acc[3];  // running maxima (bit patterns) of |v|, |v|+sqrt(gH), |J0|
+    double vp, vs, jm;    // maxima of the current state, kept by `between`
+};
+
+// Model constants (plain data, passed by value).
+struct SweConst {
+    int nx, ny;
+    int tw, th;             // HGS block: tw columns x th rows
+    int tiles_x, tiles_y;
+    int man_shift, man_w;   // Manning table: index (y >> shift) * man_w + (x >> shift)
+    int sediment_on, aj_mode, m_is_2, hgs, literal_D, nk, has_qb;
+    int nsrc;               // number of source cells
+    double g, dx, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, C_J, psi, K, dt_max, neg_tol;
+    float eps_f;            // largest float <= eps: (float)H > eps_f <=> (double)H > eps
+};
+
+// Device pointers of one solver instance.
+struct SweBufs {
+    void *buf[2];               // AoS state cells {H, Hu, Hv, b}, ping-pong
+    int *census[2];             // Index_block of K1 for state^n (census[n & 1])
+    unsigned char *skipped;     // per block: 1 = both buffers equal on the block
+    const void *gn2;            // g n^2 table (element type = state type)
+    const void *ajn;            // 0.05 n^3 table (Eq. 4 numerator)
+    const int *src_rowptr;      // ny + 1 offsets into src_x
+    const int *src_x;           // source-cell columns, grouped by row
+    const double *hyd_t, *hyd_q;
+    const void *qb;             // optional bed source per cell (state type)
+    SweDev *dev;
+    double *partials;           // diagnostics scratch: 3 doubles per block
+};
+
+// Launchers implemented per precision (swe_f32.cu / swe_f64.cu).
+namespace swe_impl {
+template <typename T> size_t step_smem_bytes(int bw);
+template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s);
+template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s);
+template <typename T> cudaError_t launch_between(const SweConst &c, const SweBufs &b, int commit, cudaStream_t s);
+template <typename T> cudaError_t launch_diag(const SweConst &c, const SweBufs &b, int nblocks, cudaStream_t s);
+template <typename T> cudaError_t launch_convert_in(const SweConst &c, void *dst, const void *H, const void *Hu,
+                                                    const void *Hv, const void *bb, int src_is_f64, cudaStream_t s);
+template <typename T> cudaError_t launch_convert_out(const SweConst &c, const void *src, void *H, void *Hu,
+                                                     void *Hv, void *bb, int dst_is_f64, cudaStream_t s);
+template <typename T> cudaError_t launch_bed_source(const SweConst &c, const SweBufs &b, cudaStream_t s);
+}  // namespace swe_impl

@@ -1,0 +1,696 @@
+// CSPH-TVD + Exner step kernels for sm_103a, templated on the state type
+// (float: production path with FP64 accumulators; double: parity build).
+//
+// Paper: Khrapov & Khoperskov (2020), Sec. 2 (Eq. 1-7) and Sec. 3 (kernels
+// K1-K8, hierarchical grid system).  The paper runs K1..K8 as eight kernels;
+// here K2-K8 are one streaming kernel per step so the state makes a single
+// HBM round trip (16 B read + 16 B write per cell in FP32):
+//
+//   * A block owns BW consecutive columns (one thread per column) and a strip
+//     of `th` rows; it writes the middle BW-8 columns (the stencil radius of
+//     one step is 4 cells: K4/K6 need radius 2, K7's reconstruction 2 more).
+//   * The block sweeps its strip row by row.  At sweep position s it loads
+//     row s, forms the particle depth H^{n+1/2} (K4) of row s-1, the forces,
+//     predictor and corrector velocities and Grass load (K2, K4-K6) of row s-2,
+//     the x- and y-face fluxes (K7) of row s-4 and updates row s-4 (K8).
+//     Intermediate rows live in small shared-memory rings, so nothing but the
+//     state itself touches HBM.
+//   * The epilogue forms, for the new state, the wet census of the block
+//     (K1's Index_block), the maxima behind the Eq. 7 time step, and a status
+//     word.  A one-thread `between` kernel turns the maxima into dt (FP64).
+//   * HGS (Sec. 3): a block is computed when it or one of its four edge
+//     neighbours holds water or a source; otherwise its state is carried over,
+//     and not even copied when both ping-pong buffers already agree.
+//
+// Ghost cells: the state is extended evenly across each wall (H, b and the
+// tangential momentum mirrored, the normal momentum negated), and every
+// derived quantity is computed on that extension with the interior formulas.
+//
+// The double instantiation evaluates every formula in the same order as the
+// FP64 CPU oracle (compiled without FMA contraction), so the two agree to a
+// few ulps per step.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "swe_internal.h"
+
+namespace swe_impl {
+
+// ------------------------------------------------------------ state cells
+
+template <typename T> struct CellIO;
+template <> struct CellIO<float> {
+    __device__ static inline void load(const void *base, long long k, float &H, float &Hu, float &Hv, float &b) {
+        float4 c = __ldg(reinterpret_cast<const float4 *>(base) + k);
+        H = c.x; Hu = c.y; Hv = c.z; b = c.w;
+    }
+    __device__ static inline void store(void *base, long long k, float H, float Hu, float Hv, float b) {
+        reinterpret_cast<float4 *>(base)[k] = make_float4(H, Hu, Hv, b);
+    }
+    __device__ static inline void copy(const void *src, void *dst, long long k) {
+        reinterpret_cast<float4 *>(dst)[k] = __ldg(reinterpret_cast<const float4 *>(src) + k);
+    }
+};
+template <> struct CellIO<double> {
+    __device__ static inline void load(const void *base, long long k, double &H, double &Hu, double &Hv, double &b) {
+        const double2 *p = reinterpret_cast<const double2 *>(base) + 2 * k;
+        double2 a = __ldg(p), c = __ldg(p + 1);
+        H = a.x; Hu = a.y; Hv = c.x; b = c.y;
+    }
+    __device__ static inline void store(void *base, long long k, double H, double Hu, double Hv, double b) {
+        double2 *p = reinterpret_cast<double2 *>(base) + 2 * k;
+        p[0] = make_double2(H, Hu);
+        p[1] = make_double2(Hv, b);
+    }
+    __device__ static inline void copy(const void *src, void *dst, long long k) {
+        const double2 *s = reinterpret_cast<const double2 *>(src) + 2 * k;
+        double2 *d = reinterpret_cast<double2 *>(dst) + 2 * k;
+        d[0] = __ldg(s);
+        d[1] = __ldg(s + 1);
+    }
+};
+
+// ------------------------------------------------------------ scalar math
+
+__device__ inline float mm_sqrt(float x) { return sqrtf(x); }
+__device__ inline double mm_sqrt(double x) { return sqrt(x); }
+// x^(4/3) for x >= eps > 0 (Manning)
+__device__ inline float pow43(float x) { return x * cbrtf(x); }
+__device__ inline double pow43(double x) { return x * cbrt(x); }
+__device__ inline float mm_pow(float x, float y) { return powf(x, y); }
+__device__ inline double mm_pow(double x, double y) { return pow(x, y); }
+__device__ inline bool mm_finite(float x) { return isfinite(x); }
+__device__ inline bool mm_finite(double x) { return isfinite(x); }
+
+// minmod limiter: 0 unless both slopes share a sign, else the smaller one.
+template <typename T> __device__ inline T minmod(T a, T b) {
+    if (a > T(0) && b > T(0)) return a < b ? a : b;
+    if (a < T(0) && b < T(0)) return a > b ? a : b;
+    return T(0);
+}
+
+// HLL flux with wave-speed bounds sL <= sR.
+template <typename T> __device__ inline T hll(T UL, T UR, T FL, T FR, T sL, T sR) {
+    if (sL >= T(0)) return FL;
+    if (sR <= T(0)) return FR;
+    return ((sR * FL - sL * FR) + (sL * sR) * (UR - UL)) / (sR - sL);
+}
+
+// wet test with FP64 semantics: (double)H > eps
+__device__ inline bool is_wet(float H, const SweConst &c) { return H > c.eps_f; }
+__device__ inline bool is_wet(double H, const SweConst &c) { return H > c.eps; }
+
+// Even extension of index i onto [0, n); sgn = -1 after an odd number of reflections.
+__device__ inline int ext_index(int i, int n, int &sgn) {
+    int period = 2 * n;
+    int p = i % period;
+    if (p < 0) p += period;
+    if (p < n) { sgn = 1; return p; }
+    sgn = -1;
+    return period - 1 - p;
+}
+
+template <typename T> struct K {  // step constants in the state precision
+    T g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol;
+    T dt, dtdx, hdt, c4, cb, dHs;
+};
+
+// Grass discharge (Eq. 3) gated by the Shamov velocity (Eq. 5, written as
+// |v|^6 > C_Sh^6 d50^2 H); A_J constant or from Eq. 4.
+template <typename T>
+__device__ inline void grass(const SweConst &c, const K<T> &k, bool wet, T H, T ajn, T vx, T vy,
+                             T &Jx, T &Jy, T &Ja) {
+    Jx = T(0); Jy = T(0); Ja = T(0);
+    if (!c.sediment_on || !wet) return;
+    T s2 = vx * vx + vy * vy;
+    if (!(s2 * s2 * s2 > k.ksh * H)) return;
+    T AJ = c.aj_mode == 1 ? ajn / ((k.sm1 * mm_sqrt(k.g * H)) * k.d50) : k.A_J;
+    T vm = c.m_is_2 ? s2 : mm_pow(s2, T(0.5) * k.m_exp);
+    Jx = (AJ * vx) * vm;
+    Jy = (AJ * vy) * vm;
+    Ja = (AJ * vm) * mm_sqrt(s2);
+}
+
+// Pressure + bed-slope force per unit mass on one axis (K2 / K5):
+// -(g/2h) (eta_p' - eta_m') * ratio, ratio = stage depth / H^n (1 at t_n,
+// H^{n+1/2}/H^n = 1/A at the half step), where a dry neighbour whose bed is
+// at or above the cell's level counts as a wall (eta' = eta).
+template <typename T>
+__device__ inline T axis_force(const K<T> &k, T ec, T ratio, T eta_p, T b_p, bool wet_p,
+                               T eta_m, T b_m, bool wet_m) {
+    T ep = (!wet_p && b_p >= ec) ? ec : eta_p;
+    T em = (!wet_m && b_m >= ec) ? ec : eta_m;
+    return -(k.coef * (ep - em)) * ratio;
+}
+
+// Limited piecewise-linear face states from the cells m, c, e, p around the
+// face c|e: left state from c, right state from e.
+template <typename T> __device__ inline void recon(const T f[4], T &L, T &R) {
+    T sc = minmod(f[1] - f[0], f[2] - f[1]);
+    T se = minmod(f[2] - f[1], f[3] - f[2]);
+    L = f[1] + T(0.5) * sc;
+    R = f[2] - T(0.5) * se;
+}
+
+// Fluxes through one face from the four cells m, c, e, p along its normal:
+// H, eta (free surface), un (normal transport velocity), wx, wy (end
+// velocity), plus the cell-centred Grass loads and beds of c and e.
+// Returns mass, x-momentum, y-momentum and Exner fluxes.
+template <typename T>
+__device__ inline void face_flux(const SweConst &c, const K<T> &k,
+                                 const T H[4], const T eta[4], const T un[4], const T wx[4], const T wy[4],
+                                 bool wet_c, bool wet_e, T Jn_c, T Jn_e, T Ja_c, T Ja_e, T b_c, T b_e,
+                                 T &Fm, T &Fx, T &Fy, T &Fj) {
+    T qL[5], qR[5];
+    recon<T>(H, qL[0], qR[0]);
+    recon<T>(eta, qL[1], qR[1]);
+    recon<T>(un, qL[2], qR[2]);
+    recon<T>(wx, qL[3], qR[3]);
+    recon<T>(wy, qL[4], qR[4]);
+    // hydrostatic face depths
+    T bL = qL[1] - qL[0], bR = qR[1] - qR[0];
+    T bf = bL > bR ? bL : bR;
+    T HL = qL[1] - bf, HR = qR[1] - bf;
+    if (!(HL > T(0))) HL = T(0);
+    if (!(HR > T(0))) HR = T(0);
+    T uL = qL[2], uR = qR[2];
+    T cL = wet_c ? mm_sqrt(k.g * HL) : T(0);
+    T cR = wet_e ? mm_sqrt(k.g * HR) : T(0);
+    T aL = uL - cL, aR = uR - cR, pL = uL + cL, pR = uR + cR;
+    T sL = aL < aR ? aL : aR, sR = pL > pR ? pL : pR;
+    Fm = hll(HL, HR, HL * uL, HR * uR, sL, sR);
+    T UxL = HL * qL[3], UxR = HR * qR[3];
+    Fx = hll(UxL, UxR, UxL * uL, UxR * uR, sL, sR);
+    T UyL = HL * qL[4], UyR = HR * qR[4];
+    Fy = hll(UyL, UyR, UyL * uL, UyR * uR, sL, sR);
+    Fj = T(0);
+    if (c.sediment_on) {
+        T su = un[1] + un[2];
+        T Jadv = su > T(0) ? Jn_c : (su < T(0) ? Jn_e : T(0));
+        Fj = Jadv - (k.cjh * (Ja_c + Ja_e)) * (b_e - b_c);
+    }
+}
+
+template <typename T> __device__ inline unsigned long long max_bits(T x);
+template <> __device__ inline unsigned long long max_bits<float>(float x) { return (unsigned long long)__float_as_uint(x); }
+template <> __device__ inline unsigned long long max_bits<double>(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+template <typename T> __device__ inline T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) { T w = __shfl_xor_sync(0xffffffffu, v, o); v = w > v ? w : v; }
+    return v;
+}
+__device__ inline int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T> __device__ inline void atomic_max_acc(unsigned long long *a, T v);
+template <> __device__ inline void atomic_max_acc<float>(unsigned long long *a, float v) {
+    atomicMax(a, (unsigned long long)__float_as_uint(v));
+}
+template <> __device__ inline void atomic_max_acc<double>(unsigned long long *a, double v) {
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// --------------------------------------------------------- block epilogue
+
+template <typename T, int BW>
+__device__ inline void block_finish(int cnt, T m0, T m1, T m2, unsigned st, int tile,
+                                    int *census_out, SweDev *dev, int count_active) {
+    __shared__ int s_cnt[BW / 32];
+    __shared__ T s_m[3][BW / 32];
+    __shared__ unsigned s_st[BW / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    cnt = warp_sum(cnt);
+    m0 = warp_max(m0); m1 = warp_max(m1); m2 = warp_max(m2);
+    st = __reduce_or_sync(0xffffffffu, st);
+    if (lane == 0) { s_cnt[wid] = cnt; s_m[0][wid] = m0; s_m[1][wid] = m1; s_m[2][wid] = m2; s_st[wid] = st; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tc = 0; T a = T(0), b = T(0), c = T(0); unsigned s = 0;
+        for (int w = 0; w < BW / 32; ++w) {
+            tc += s_cnt[w];
+            a = s_m[0][w] > a ? s_m[0][w] : a;
+            b = s_m[1][w] > b ? s_m[1][w] : b;
+            c = s_m[2][w] > c ? s_m[2][w] : c;
+            s |= s_st[w];
+        }
+        census_out[tile] = tc;
+        if (a > T(0)) atomic_max_acc<T>(&dev->acc[0], a);
+        if (b > T(0)) atomic_max_acc<T>(&dev->acc[1], b);
+        if (c > T(0)) atomic_max_acc<T>(&dev->acc[2], c);
+        if (s) atomicOr(&dev->status, s);
+        if (count_active) atomicAdd(&dev->active_tiles, 1);
+    }
+}
+
+// Per-cell terms of Eq. 7 and the census for a new state value.
+template <typename T>
+__device__ inline void cell_epilogue(const SweConst &c, const K<T> &k, T hn, T hun, T hvn, T bn, T ajn,
+                                     bool src, int &cnt, T &m0, T &m1, T &m2, unsigned &st) {
+    bool wet = is_wet(hn, c);
+    cnt += (wet || src) ? 1 : 0;
+    if (wet) {
+        T u = hun / hn, v = hvn / hn;
+        T va = mm_sqrt(u * u + v * v);
+        T cs = va + mm_sqrt(k.g * hn);
+        m0 = va > m0 ? va : m0;
+        m1 = cs > m1 ? cs : m1;
+        T jx, jy, ja;
+        grass<T>(c, k, true, hn, ajn, u, v, jx, jy, ja);
+        m2 = ja > m2 ? ja : m2;
+    }
+    if (!(hn >= -k.neg_tol)) st |= 2u;
+    if (!mm_finite(hn) || !mm_finite(bn) || !mm_finite(hun) || !mm_finite(hvn)) st |= 1u;
+}
+
+template <typename T> __device__ inline K<T> load_k(const SweConst &c, const SweDev *dev) {
+    K<T> k;
+    k.g = T(c.g); k.eps = T(c.eps); k.coef = T(c.coef); k.cjh = T(c.cjh); k.ksh = T(c.ksh);
+    k.A_J = T(c.A_J); k.m_exp = T(c.m_exp); k.sm1 = T(c.sm1); k.d50 = T(c.d50); k.neg_tol = T(c.neg_tol);
+    k.dt = T(dev->dt); k.dtdx = T(dev->dtdx); k.hdt = T(dev->hdt); k.c4 = T(dev->c4); k.cb = T(dev->cb);
+    k.dHs = T(dev->dHs);
+    return k;
+}
+
+// ---------------------------------------------------------- step kernel
+
+// Shared-memory rings (each row padded by 2 entries on both sides so the
+// edge threads' out-of-block neighbour reads stay in bounds; those threads'
+// results are never used).
+template <typename T, int BW> struct StepSmem {
+    static constexpr int RW = BW + 4;
+    T H[8][RW], b[8][RW], u[8][RW], v[8][RW];       // state ring (rows s-7..s)
+    T Hh[4][RW];                                    // K4 particle depth ring
+    T ux[4][RW], uy[4][RW], wx[4][RW], wy[4][RW];   // K4/K6 velocity rings
+    T jx[4][RW], jy[4][RW], ja[4][RW];              // Grass load ring
+    T F[4][RW];                                     // x-face fluxes of the update row
+};
+
+template <typename T> __device__ inline T tab(const void *p, int i) { return reinterpret_cast<const T *>(p)[i]; }
+
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW) step_kernel(SweConst c, SweBufs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
+    SweDev *dev = B.dev;
+    if (!dev->scheduled) return;
+    const int t = threadIdx.x;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int tile = by * c.tiles_x + bx;
+    const long long n = dev->n;
+    const int par = (int)(n & 1);
+    const void *in = par ? B.buf[1] : B.buf[0];
+    void *out = par ? B.buf[0] : B.buf[1];
+    const int *cen_in = par ? B.census[1] : B.census[0];
+    int *cen_out = par ? B.census[0] : B.census[1];
+    const int tx0 = bx * c.tw;                       // first output column
+    const int y0 = by * c.th, y1 = min(y0 + c.th, c.ny);
+
+    // ---- K1 / HGS: skip dry blocks (Sec. 3, kernel_ES rule: the block or one
+    // of its four edge neighbours must hold water)
+    if (c.hgs) {
+        int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
+        int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
+        bool active = cen_in[tile] > 0 || cen_in[by * c.tiles_x + l] > 0 || cen_in[by * c.tiles_x + r] > 0 ||
+                      cen_in[d * c.tiles_x + bx] > 0 || cen_in[u * c.tiles_x + bx] > 0;
+        if (!active) {
+            if (!B.skipped[tile]) {
+                int x1 = min(tx0 + c.tw, c.nx);
+                for (int y = y0; y < y1; ++y)
+                    for (int x = tx0 + t; x < x1; x += BW) CellIO<T>::copy(in, out, (long long)y * c.nx + x);
+            }
+            if (t == 0) {
+                if (!B.skipped[tile])
+                    atomicAdd(&dev->cells_copied, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
+                cen_out[tile] = 0;
+                B.skipped[tile] = 1;
+            }
+            return;
+        }
+        if (t == 0) B.skipped[tile] = 0;
+    }
+    if (t == 0) atomicAdd(&dev->cells_computed, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
+
+    const K<T> k = load_k<T>(c, dev);
+    const int x = tx0 - 4 + t;                       // this thread's column
+    int sx;
+    const int xx = ext_index(x, c.nx, sx);
+    const T sxT = T(sx);
+    const int mrow_x = xx >> c.man_shift;
+    const bool out_lane = (t >= 4) && (t < BW - 4) && (x < c.nx);
+    const int o = t + 2;                             // padded smem index
+
+    // y-face fluxes of the previous sweep position (south face of the update row)
+    T GS0 = T(0), GS1 = T(0), GS2 = T(0), GS3 = T(0);
+    int cnt = 0;
+    T m0 = T(0), m1 = T(0), m2 = T(0);
+    unsigned st = 0;
+
+    // prefetch distance 2: a two-deep register shift (rows s and s+1)
+    T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
+    int asy, bsy;
+    {
+        int yy = ext_index(y0 - 4, c.ny, asy);
+        CellIO<T>::load(in, (long long)yy * c.nx + xx, aH, aHu, aHv, ab);
+        yy = ext_index(y0 - 3, c.ny, bsy);
+        CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+    }
+
+    for (int s = y0 - 4; s <= y1 + 3; ++s) {
+        // ---------------- load row s (ghost rows by even extension)
+        {
+            const T H = aH, Hu = aHu, Hv = aHv, bb = ab;
+            const T syT = T(asy);
+            aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
+            if (s + 2 <= y1 + 3) {
+                int yy = ext_index(s + 2, c.ny, bsy);
+                CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+            }
+            const bool wet = is_wet(H, c);
+            const int r8 = s & 7;
+            S.H[r8][o] = H;
+            S.b[r8][o] = bb;
+            S.u[r8][o] = wet ? (sxT * Hu) / H : T(0);
+            S.v[r8][o] = wet ? (syT * Hv) / H : T(0);
+        }
+        __syncthreads();
+        // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
+        if (s - 1 >= y0 - 3) {
+            const int r = s - 1, r8 = r & 7;
+            T A = T(1) + k.c4 * ((S.u[r8][o + 1] - S.u[r8][o - 1]) + (S.v[(r + 1) & 7][o] - S.v[(r - 1) & 7][o]));
+            S.Hh[r & 3][o] = S.H[r8][o] / A;
+        }
+        __syncthreads();
+        // ---------------- K2, K4, K5, K6 and Grass load, row s-2
+        if (s - 2 >= y0 - 2) {
+            const int r = s - 2, r8 = r & 7, rn = (r + 1) & 7, rs = (r - 1) & 7;
+            const int a4 = r & 3, an = (r + 1) & 3, as = (r - 1) & 3;
+            const T Hc = S.H[r8][o], bc = S.b[r8][o], u = S.u[r8][o], v = S.v[r8][o];
+            const bool wet = is_wet(Hc, c);
+            int sy;
+            const int yy = ext_index(r, c.ny, sy);
+            const int mi = (yy >> c.man_shift) * c.man_w + mrow_x;
+            const T gn2 = tab<T>(B.gn2, mi);
+            T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0);
+            {
+                // K2: forces at t_n
+                T ax = T(0), ay = T(0);
+                const T ec = Hc + bc;
+                if (wet) {
+                    const T HE = S.H[r8][o + 1], bE = S.b[r8][o + 1];
+                    const T HW = S.H[r8][o - 1], bW = S.b[r8][o - 1];
+                    const T HN = S.H[rn][o], bN = S.b[rn][o];
+                    const T HS = S.H[rs][o], bS = S.b[rs][o];
+                    ax = axis_force<T>(k, ec, T(1), HE + bE, bE, is_wet(HE, c), HW + bW, bW, is_wet(HW, c));
+                    ay = axis_force<T>(k, ec, T(1), HN + bN, bN, is_wet(HN, c), HS + bS, bS, is_wet(HS, c));
+                }
+                // K4: predictor velocity with point-implicit Manning at |v^n|
+                const T Hm = wet ? Hc : k.eps;
+                const T cf = gn2 / pow43(Hm);
+                const T va = mm_sqrt(u * u + v * v);
+                const T den = T(1) + k.hdt * (cf * va);
+                vtx = (u + k.hdt * ax) / den;
+                vty = (v + k.hdt * ay) / den;
+                // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
+                T bxf = T(0), byf = T(0);
+                if (wet) {
+                    const T hc = S.Hh[a4][o], ech = hc + bc;
+                    const T hE = S.Hh[a4][o + 1], bE = S.b[r8][o + 1], HE = S.H[r8][o + 1];
+                    const T hW = S.Hh[a4][o - 1], bW = S.b[r8][o - 1], HW = S.H[r8][o - 1];
+                    const T hN = S.Hh[an][o], bN = S.b[rn][o], HN = S.H[rn][o];
+                    const T hS = S.Hh[as][o], bS = S.b[rs][o], HS = S.H[rs][o];
+                    const T ratio = hc / Hc;
+                    bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, is_wet(HE, c), hW + bW, bW, is_wet(HW, c));
+                    byf = axis_force<T>(k, ech, ratio, hN + bN, bN, is_wet(HN, c), hS + bS, bS, is_wet(HS, c));
+                }
+                // K6: corrector (Lagrangian end) velocity with Manning at |vt|
+                const T vat = mm_sqrt(vtx * vtx + vty * vty);
+                const T den2 = T(1) + k.dt * (cf * vat);
+                wxv = (u + k.dt * bxf) / den2;
+                wyv = (v + k.dt * byf) / den2;
+            }
+            S.ux[a4][o] = vtx; S.uy[a4][o] = vty; S.wx[a4][o] = wxv; S.wy[a4][o] = wyv;
+            T jx, jy, ja;
+            grass<T>(c, k, wet, Hc, tab<T>(B.ajn, mi), vtx, vty, jx, jy, ja);
+            S.jx[a4][o] = jx; S.jy[a4][o] = jy; S.ja[a4][o] = ja;
+        }
+        __syncthreads();
+        // ---------------- K7: fluxes of row s-4 (x-face t|t+1) and the y-face (s-4 | s-3)
+        T GN0 = T(0), GN1 = T(0), GN2 = T(0), GN3 = T(0);
+        const bool upd = (s - 4 >= y0);
+        if (s - 3 >= y0) {
+            const int r = s - 4;
+            if (upd) {
+                const int r8 = r & 7, a4 = r & 3;
+                T Hq[4], eq[4], uq[4], wxq[4], wyq[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int oj = o - 1 + j;
+                    Hq[j] = S.H[r8][oj]; eq[j] = Hq[j] + S.b[r8][oj];
+                    uq[j] = S.ux[a4][oj]; wxq[j] = S.wx[a4][oj]; wyq[j] = S.wy[a4][oj];
+                }
+                T f0, f1, f2, f3;
+                face_flux<T>(c, k, Hq, eq, uq, wxq, wyq, is_wet(Hq[1], c), is_wet(Hq[2], c),
+                             S.jx[a4][o], S.jx[a4][o + 1], S.ja[a4][o], S.ja[a4][o + 1],
+                             S.b[r8][o], S.b[r8][o + 1], f0, f1, f2, f3);
+                S.F[0][o] = f0; S.F[1][o] = f1; S.F[2][o] = f2; S.F[3][o] = f3;
+            }
+            // y-face between rows r and r+1 of this column
+            T Hq[4], eq[4], uq[4], wxq[4], wyq[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int rr = r - 1 + j;
+                Hq[j] = S.H[rr & 7][o]; eq[j] = Hq[j] + S.b[rr & 7][o];
+                uq[j] = S.uy[rr & 3][o]; wxq[j] = S.wx[rr & 3][o]; wyq[j] = S.wy[rr & 3][o];
+            }
+            face_flux<T>(c, k, Hq, eq, uq, wxq, wyq, is_wet(Hq[1], c), is_wet(Hq[2], c),
+                         S.jy[r & 3][o], S.jy[(r + 1) & 3][o], S.ja[r & 3][o], S.ja[(r + 1) & 3][o],
+                         S.b[r & 7][o], S.b[(r + 1) & 7][o], GN0, GN1, GN2, GN3);
+        }
+        __syncthreads();
+        // ---------------- K8: update row s-4
+        if (upd) {
+            const int r = s - 4, r8 = r & 7, a4 = r & 3;
+            if (out_lane) {
+                const T Hc = S.H[r8][o], bc = S.b[r8][o];
+                bool src = false;
+                for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
+                T hn = Hc - k.dtdx * ((S.F[0][o] - S.F[0][o - 1]) + (GN0 - GS0));
+                if (src) hn = hn + k.dHs;
+                T hun = Hc * S.wx[a4][o] - k.dtdx * ((S.F[1][o] - S.F[1][o - 1]) + (GN1 - GS1));
+                T hvn = Hc * S.wy[a4][o] - k.dtdx * ((S.F[2][o] - S.F[2][o - 1]) + (GN2 - GS2));
+                if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
+                const T bn = bc - k.cb * ((S.F[3][o] - S.F[3][o - 1]) + (GN3 - GS3));
+                const long long kk = (long long)r * c.nx + x;
+                CellIO<T>::store(out, kk, hn, hun, hvn, bn);
+                const int mi = (r >> c.man_shift) * c.man_w + mrow_x;
+                cell_epilogue<T>(c, k, hn, hun, hvn, bn, tab<T>(B.ajn, mi), src, cnt, m0, m1, m2, st);
+            }
+        }
+        GS0 = GN0; GS1 = GN1; GS2 = GN2; GS3 = GN3;
+    }
+    block_finish<T, BW>(cnt, m0, m1, m2, st, tile, cen_out, dev, 1);
+}
+
+// ----------------------------------------------- census + Eq. 7 terms of a state
+
+// Canonicalises a freshly set state (dry cells carry no momentum) and forms
+// the census and the Eq. 7 maxima for it.  One block per HGS tile.
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW) init_kernel(SweConst c, SweBufs B) {
+    SweDev *dev = B.dev;
+    const long long n = dev->n;
+    void *buf = (n & 1) ? B.buf[1] : B.buf[0];
+    const int bx = blockIdx.x, by = blockIdx.y, tile = by * c.tiles_x + bx;
+    const int x0 = bx * c.tw, y0 = by * c.th;
+    const int x1 = min(x0 + c.tw, c.nx), y1 = min(y0 + c.th, c.ny);
+    K<T> k;
+    k.g = T(c.g); k.eps = T(c.eps); k.ksh = T(c.ksh); k.A_J = T(c.A_J); k.m_exp = T(c.m_exp);
+    k.sm1 = T(c.sm1); k.d50 = T(c.d50); k.neg_tol = T(c.neg_tol);
+    int cnt = 0;
+    T m0 = T(0), m1 = T(0), m2 = T(0);
+    unsigned st = 0;
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0 + (int)threadIdx.x; x < x1; x += BW) {
+            long long kk = (long long)y * c.nx + x;
+            T H, Hu, Hv, bb;
+            CellIO<T>::load(buf, kk, H, Hu, Hv, bb);
+            if (!is_wet(H, c)) { Hu = T(0); Hv = T(0); CellIO<T>::store(buf, kk, H, Hu, Hv, bb); }
+            bool src = false;
+            for (int q = B.src_rowptr[y]; q < B.src_rowptr[y + 1]; ++q) src |= (B.src_x[q] == x);
+            int mi = (y >> c.man_shift) * c.man_w + (x >> c.man_shift);
+            cell_epilogue<T>(c, k, H, Hu, Hv, bb, tab<T>(B.ajn, mi), src, cnt, m0, m1, m2, st);
+        }
+    block_finish<T, BW>(cnt, m0, m1, m2, st, tile, (n & 1) ? B.census[1] : B.census[0], dev, 0);
+    if (threadIdx.x == 0) B.skipped[tile] = 0;
+}
+
+// ------------------------------------------------------ dt (K3) and bookkeeping
+
+// Piecewise-linear hydrograph integral over [ta, tb] (constant beyond the ends).
+__device__ inline double hydro_integral(int nk, const double *tk, const double *Qk, double ta, double tb) {
+    if (nk <= 0 || !(tb > ta)) return 0.0;
+    double s = 0.0;
+    if (ta < tk[0]) { double e = tb < tk[0] ? tb : tk[0]; s += Qk[0] * (e - ta); }
+    for (int j = 0; j + 1 < nk; ++j) {
+        double a = ta > tk[j] ? ta : tk[j];
+        double b = tb < tk[j + 1] ? tb : tk[j + 1];
+        if (!(b > a)) continue;
+        double span = tk[j + 1] - tk[j];
+        double qa = Qk[j] + (Qk[j + 1] - Qk[j]) * ((a - tk[j]) / span);
+        double qb = Qk[j] + (Qk[j + 1] - Qk[j]) * ((b - tk[j]) / span);
+        s += 0.5 * (qa + qb) * (b - a);
+    }
+    if (tb > tk[nk - 1]) { double a = ta > tk[nk - 1] ? ta : tk[nk - 1]; s += Qk[nk - 1] * (tb - a); }
+    return s;
+}
+
+template <typename T> __device__ inline double acc_value(unsigned long long bits);
+template <> __device__ inline double acc_value<float>(unsigned long long bits) { return (double)__uint_as_float((unsigned)bits); }
+template <> __device__ inline double acc_value<double>(unsigned long long bits) { return __longlong_as_double((long long)bits); }
+
+// One thread.  mode 1 (commit) first commits the step that just ran, if one
+// was scheduled (n += 1, t += dt, the maxima gathered by its epilogue become
+// the current ones); mode 2 (init) takes the maxima the census kernel
+// gathered for a freshly set state; mode 0 only re-prepares.  It then forms
+// dt of the next step from Eq. 7 (FP64), clipped to t_end - t, the source
+// increment and the step coefficients.
+template <typename T>
+__global__ void between_kernel(SweConst c, SweBufs B, int mode) {
+    SweDev *d = B.dev;
+    const int nsrc = c.nsrc;
+    bool take = mode == 2;
+    if (mode == 1 && d->scheduled) {
+        d->n += 1;
+        d->t = d->binding == 4 ? d->t_end : d->t + d->dt;  // a clipped step lands on t_end
+        d->dt_last = d->dt;
+        d->binding_last = d->binding;
+        d->inflow_total += d->dHs * ((double)nsrc * (c.dx * c.dx));
+        d->active_last = d->active_tiles;
+        take = true;
+    }
+    if (take) {
+        d->vp = acc_value<T>(d->acc[0]);
+        d->vs = acc_value<T>(d->acc[1]);
+        d->jm = acc_value<T>(d->acc[2]);
+        d->acc[0] = 0ull; d->acc[1] = 0ull; d->acc[2] = 0ull;
+    }
+    const double h = c.dx;
+    double best = INFINITY;
+    int which = 3;
+    if (d->vp > 0.0) { double a = h / (2.0 * d->vp); if (a < best) { best = a; which = 0; } }
+    if (d->vs > 0.0) { double a = h / d->vs; if (a < best) { best = a; which = 1; } }
+    if (c.sediment_on && d->jm > 0.0) {
+        double D = (c.literal_D ? d->jm : c.C_J * d->jm) / (1.0 - c.psi);
+        double a = (h * h) / (2.0 * D);
+        if (a < best) { best = a; which = 2; }
+    }
+    double dt = c.K * best;
+    if (!(dt < c.dt_max)) { dt = c.dt_max; which = 3; }
+    d->dt_unclipped = dt;
+    if (d->t_end < INFINITY) {
+        double rem = d->t_end - d->t;
+        if (!(rem > 0.0)) { dt = 0.0; d->done = 1; }
+        else if (rem < dt) { dt = rem; which = 4; }
+    }
+    d->dt = dt;
+    d->binding = which;
+    d->scheduled = dt > 0.0 ? 1 : 0;
+    double vol = (nsrc > 0 && dt > 0.0) ? hydro_integral(c.nk, B.hyd_t, B.hyd_q, d->t, d->t + dt) : 0.0;
+    d->dHs = nsrc > 0 ? vol / ((double)nsrc * (c.dx * c.dx)) : 0.0;
+    d->dtdx = dt / c.dx;
+    d->hdt = 0.5 * dt;
+    d->c4 = dt / (4.0 * c.dx);
+    d->cb = d->dtdx / (1.0 - c.psi);
+    d->active_tiles = 0;
+}
+
+// b += dt q / (1 - psi) on the freshly written buffer (Eq. 1 bed source).
+template <typename T>
+__global__ void bed_source_kernel(SweConst c, SweBufs B) {
+    SweDev *d = B.dev;
+    if (!d->scheduled) return;
+    void *out = ((d->n + 1) & 1) ? B.buf[1] : B.buf[0];
+    const T cq = T(d->dt / (1.0 - c.psi));
+    const long long N = (long long)c.nx * c.ny;
+    for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < N; kk += (long long)gridDim.x * blockDim.x) {
+        T H, Hu, Hv, bb;
+        CellIO<T>::load(out, kk, H, Hu, Hv, bb);
+        bb = bb + cq * tab<T>(B.qb, (int)kk);
+        CellIO<T>::store(out, kk, H, Hu, Hv, bb);
+    }
+}
+
+// ------------------------------------------------------------ diagnostics
+
+// FP64 sums of H and b and the wet count, in a fixed order: per-block
+// partials here, then a one-block pass.
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW) diag_partial_kernel(SweConst c, SweBufs B) {
+    const void *buf = (B.dev->n & 1) ? B.buf[1] : B.buf[0];
+    const long long N = (long long)c.nx * c.ny;
+    double sh = 0.0, sb = 0.0, sw = 0.0;
+    for (long long kk = blockIdx.x * (long long)BW + threadIdx.x; kk < N; kk += (long long)gridDim.x * BW) {
+        T H, Hu, Hv, bb;
+        CellIO<T>::load(buf, kk, H, Hu, Hv, bb);
+        sh += (double)H; sb += (double)bb; sw += is_wet(H, c) ? 1.0 : 0.0;
+    }
+    __shared__ double r[3][BW];
+    r[0][threadIdx.x] = sh; r[1][threadIdx.x] = sb; r[2][threadIdx.x] = sw;
+    __syncthreads();
+    for (int w = BW / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) r[q][threadIdx.x] += r[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) B.partials[3 * blockIdx.x + q] = r[q][0];
+}
+
+__global__ void diag_final_kernel(SweBufs B, int nblocks, double *out3);
+
+// ------------------------------------------------------------ conversion
+
+template <typename T>
+__global__ void convert_in_kernel(SweConst c, void *dst, const void *H, const void *Hu, const void *Hv,
+                                  const void *bb, int f64) {
+    const long long N = (long long)c.nx * c.ny;
+    for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < N; kk += (long long)gridDim.x * blockDim.x) {
+        T a, b2, c2, d2;
+        if (f64) {
+            a = T(((const double *)H)[kk]); b2 = T(((const double *)Hu)[kk]);
+            c2 = T(((const double *)Hv)[kk]); d2 = T(((const double *)bb)[kk]);
+        } else {
+            a = T(((const float *)H)[kk]); b2 = T(((const float *)Hu)[kk]);
+            c2 = T(((const float *)Hv)[kk]); d2 = T(((const float *)bb)[kk]);
+        }
+        CellIO<T>::store(dst, kk, a, b2, c2, d2);
+    }
+}
+
+template <typename T>
+__global__ void convert_out_kernel(SweConst c, const void *src, void *H, void *Hu, void *Hv, void *bb, int f64) {
+    const long long N = (long long)c.nx * c.ny;
+    for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < N; kk += (long long)gridDim.x * blockDim.x) {
+        T a, b2, c2, d2;
+        CellIO<T>::load(src, kk, a, b2, c2, d2);
+        if (f64) {
+            if (H) ((double *)H)[kk] = (double)a;
+            if (Hu) ((double *)Hu)[kk] = (double)b2;
+            if (Hv) ((double *)Hv)[kk] = (double)c2;
+            if (bb) ((double *)bb)[kk] = (double)d2;
+        } else {
+            if (H) ((float *)H)[kk] = (float)a;
+            if (Hu) ((float *)Hu)[kk] = (float)b2;
+            if (Hv) ((float *)Hv)[kk] = (float)c2;
+            if (bb) ((float *)bb)[kk] = (float)d2;
+        }
+    }
+}
+
+}  // namespace swe_impl

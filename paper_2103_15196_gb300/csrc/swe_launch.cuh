@@ -1,0 +1,80 @@
+// Generic launchers; each precision's translation unit includes this file and
+// instantiates the templates for its own state type.
+#pragma once
+#include "swe_kernels.cuh"
+
+namespace swe_impl {
+
+template <typename T> size_t step_smem_bytes(int bw) {
+    return bw == 128 ? sizeof(StepSmem<T, 128>) : sizeof(StepSmem<T, 256>);
+}
+
+template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+    static bool configured = false;
+    const size_t smem = sizeof(StepSmem<T, BW>);
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid(c.tiles_x, c.tiles_y);
+    step_kernel<T, BW><<<grid, BW, smem, s>>>(c, b);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s) {
+    if (bw == 128) return launch_step_bw<T, 128>(c, b, s);
+    return launch_step_bw<T, 256>(c, b, s);
+}
+
+template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+    dim3 grid(c.tiles_x, c.tiles_y);
+    init_kernel<T, 256><<<grid, 256, 0, s>>>(c, b);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_between(const SweConst &c, const SweBufs &b, int commit, cudaStream_t s) {
+    between_kernel<T><<<1, 1, 0, s>>>(c, b, commit);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_diag(const SweConst &c, const SweBufs &b, int nblocks, cudaStream_t s) {
+    diag_partial_kernel<T, 256><<<nblocks, 256, 0, s>>>(c, b);
+    return cudaGetLastError();
+}
+
+static inline int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
+}
+
+template <typename T> cudaError_t launch_convert_in(const SweConst &c, void *dst, const void *H, const void *Hu,
+                                                    const void *Hv, const void *bb, int f64, cudaStream_t s) {
+    convert_in_kernel<T><<<grid_for((long long)c.nx * c.ny), 256, 0, s>>>(c, dst, H, Hu, Hv, bb, f64);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_convert_out(const SweConst &c, const void *src, void *H, void *Hu,
+                                                     void *Hv, void *bb, int f64, cudaStream_t s) {
+    convert_out_kernel<T><<<grid_for((long long)c.nx * c.ny), 256, 0, s>>>(c, src, H, Hu, Hv, bb, f64);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_bed_source(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+    bed_source_kernel<T><<<grid_for((long long)c.nx * c.ny), 256, 0, s>>>(c, b);
+    return cudaGetLastError();
+}
+
+#define SWE_INSTANTIATE(T)                                                                                        \
+    template size_t step_smem_bytes<T>(int);                                                                      \
+    template cudaError_t launch_step<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                   \
+    template cudaError_t launch_init<T>(const SweConst &, const SweBufs &, cudaStream_t);                        \
+    template cudaError_t launch_between<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                \
+    template cudaError_t launch_diag<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                   \
+    template cudaError_t launch_convert_in<T>(const SweConst &, void *, const void *, const void *, const void *, \
+                                              const void *, int, cudaStream_t);                                   \
+    template cudaError_t launch_convert_out<T>(const SweConst &, const void *, void *, void *, void *, void *,   \
+                                               int, cudaStream_t);                                                \
+    template cudaError_t launch_bed_source<T>(const SweConst &, const SweBufs &, cudaStream_t);
+
+}  // namespace swe_impl

@@ -1,0 +1,261 @@
+"""Python binding of the C ABI in ``include/swe.h`` (argument marshalling only).
+
+Every step of the CSPH-TVD + Exner method runs in the CUDA kernels of the
+in-tree library ``_lib/libswe.so``; this module converts numpy arrays or
+torch CUDA tensors to pointers and status codes to exceptions.  There is no
+CPU fallback: if the library cannot be built or loaded, ``load_library``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+SWE_OK, SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA, SWE_ENUMERIC, SWE_ETIMEOUT, SWE_ESTATE = range(7)
+SWE_FP64, SWE_FP32 = 0, 1
+SWE_HOST, SWE_DEVICE = 0, 1
+STATUS_NAMES = {0: "SWE_OK", 1: "SWE_EINVAL", 2: "SWE_ENOMEM", 3: "SWE_ECUDA", 4: "SWE_ENUMERIC",
+                5: "SWE_ETIMEOUT", 6: "SWE_ESTATE"}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "swe.h")
+
+
+class SweError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("g", ctypes.c_double),
+        ("cfl_K", ctypes.c_double), ("eps_wet", ctypes.c_double), ("dt_max", ctypes.c_double),
+        ("psi", ctypes.c_double), ("sediment_on", ctypes.c_int), ("aj_mode", ctypes.c_int),
+        ("A_J", ctypes.c_double), ("m_exp", ctypes.c_double), ("C_J", ctypes.c_double),
+        ("d50", ctypes.c_double), ("s_rel", ctypes.c_double), ("C_Sh", ctypes.c_double),
+        ("dt_literal_D", ctypes.c_int), ("precision", ctypes.c_int), ("hgs_skip", ctypes.c_int),
+        ("tile_rows", ctypes.c_int), ("block_cols", ctypes.c_int), ("neg_tol", ctypes.c_double),
+    ]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("dt_next", ctypes.c_double),
+        ("binding", ctypes.c_int), ("water_volume", ctypes.c_double),
+        ("sediment_volume", ctypes.c_double), ("inflow_volume", ctypes.c_double),
+        ("steps", ctypes.c_int64), ("wet_cells", ctypes.c_int64), ("active_tiles", ctypes.c_int32),
+        ("total_tiles", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+        ("status", ctypes.c_uint32), ("cells_computed", ctypes.c_uint64),
+        ("cells_copied", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions the public header declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:swe_status|const char \*)\s*(swe_\w+)\s*\(", txt, re.M)))
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads (building it first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    H = ctypes.c_void_p
+    sig = {
+        "swe_params_default": [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, ctypes.c_double],
+        "swe_create": [ctypes.POINTER(Params), vp, ctypes.POINTER(H)],
+        "swe_destroy": [H],
+        "swe_set_manning": [H, dp, ctypes.c_int],
+        "swe_set_sources": [H, ctypes.POINTER(ctypes.c_uint8), dp, dp, ctypes.c_int],
+        "swe_set_bed_source": [H, dp],
+        "swe_set_state": [H, dp, dp, dp, dp],
+        "swe_set_state_ex": [H, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int],
+        "swe_get_state": [H, dp, dp, dp, dp],
+        "swe_get_state_ex": [H, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int],
+        "swe_step": [H, dp],
+        "swe_advance": [H, ctypes.c_double, i64p],
+        "swe_run_steps": [H, ctypes.c_int64],
+        "swe_sync": [H],
+        "swe_get_time": [H, dp],
+        "swe_set_time": [H, ctypes.c_double],
+        "swe_get_diag": [H, ctypes.POINTER(Diag)],
+        "swe_get_census": [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.swe_last_error.argtypes = [H]
+    L.swe_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One CSPH-TVD + Exner grid on the current CUDA device.
+
+    precision: 'fp32' (FP32 state, FP64 dt/accumulators) or 'fp64'.
+    Other keyword arguments override fields of ``swe_params``."""
+
+    def __init__(self, nx, ny, dx, precision="fp32", stream=None, **kw):
+        L = load_library()
+        self._L = L
+        p = Params()
+        self._check(L.swe_params_default(ctypes.byref(p), nx, ny, dx), None)
+        p.precision = SWE_FP32 if precision == "fp32" else SWE_FP64
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        self.nx, self.ny, self.dx = nx, ny, dx
+        self.precision = precision
+        h = ctypes.c_void_p()
+        st = L.swe_create(ctypes.byref(p), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if st != SWE_OK:
+            raise SweError(st, "swe_create failed")
+        self._h = h
+
+    def _check(self, st, h="self"):
+        if st != SWE_OK:
+            msg = self._L.swe_last_error(self._h).decode() if h == "self" else ""
+            raise SweError(st, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.swe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ inputs
+    def set_manning(self, n, block=0):
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        self._check(self._L.swe_set_manning(self._h, _ptr(n), int(block)))
+
+    def set_sources(self, mask, t=None, Q=None):
+        if mask is None:
+            self._check(self._L.swe_set_sources(self._h, None, None, None, 0))
+            return
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        assert m.shape == (self.ny, self.nx)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        self._check(self._L.swe_set_sources(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                            _ptr(t), _ptr(Q), len(t)))
+
+    def set_bed_source(self, q):
+        if q is None:
+            self._check(self._L.swe_set_bed_source(self._h, None))
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            self._check(self._L.swe_set_bed_source(self._h, _ptr(q)))
+
+    def set_state(self, H, Hu, Hv, b):
+        """Host numpy arrays (float64 or float32) or torch CUDA tensors."""
+        arrs = [H, Hu, Hv, b]
+        if _is_torch(H):
+            import torch
+            ts = [a.contiguous() for a in arrs]
+            dt = SWE_FP64 if ts[0].dtype == torch.float64 else SWE_FP32
+            ts = [a.to(ts[0].dtype) for a in ts]
+            torch.cuda.current_stream().synchronize()
+            self._check(self._L.swe_set_state_ex(self._h, *[ctypes.c_void_p(a.data_ptr()) for a in ts],
+                                                 dt, SWE_DEVICE))
+            return
+        dtype = np.float32 if np.asarray(H).dtype == np.float32 else np.float64
+        arrs = [np.ascontiguousarray(a, dtype=dtype) for a in arrs]
+        for a in arrs:
+            assert a.shape == (self.ny, self.nx), a.shape
+        self._check(self._L.swe_set_state_ex(self._h, *[ctypes.c_void_p(a.ctypes.data) for a in arrs],
+                                             SWE_FP64 if dtype == np.float64 else SWE_FP32, SWE_HOST))
+
+    def get_state(self, dtype=np.float64, out=None):
+        """Host copy of (H, Hu, Hv, b); `out` may supply four C-contiguous arrays."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx), dtype=dtype) for _ in range(4)]
+        dtype = out[0].dtype
+        self._check(self._L.swe_get_state_ex(self._h, *[ctypes.c_void_p(a.ctypes.data) for a in out],
+                                             SWE_FP64 if dtype == np.float64 else SWE_FP32, SWE_HOST))
+        return out
+
+    def get_state_device(self, tensors):
+        import torch
+        dt = SWE_FP64 if tensors[0].dtype == torch.float64 else SWE_FP32
+        self._check(self._L.swe_get_state_ex(self._h, *[ctypes.c_void_p(a.data_ptr()) for a in tensors],
+                                             dt, SWE_DEVICE))
+
+    # ------------------------------------------------------------ stepping
+    def step(self):
+        dt = ctypes.c_double(0.0)
+        self._check(self._L.swe_step(self._h, ctypes.byref(dt)))
+        return dt.value
+
+    def advance(self, t_end):
+        n = ctypes.c_int64(0)
+        self._check(self._L.swe_advance(self._h, float(t_end), ctypes.byref(n)))
+        return n.value
+
+    def run_steps(self, n):
+        self._check(self._L.swe_run_steps(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.swe_sync(self._h))
+
+    @property
+    def t(self):
+        v = ctypes.c_double(0.0)
+        self._check(self._L.swe_get_time(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_time(self, t):
+        self._check(self._L.swe_set_time(self._h, float(t)))
+
+    def diag(self):
+        d = Diag()
+        self._check(self._L.swe_get_diag(self._h, ctypes.byref(d)))
+        return d.as_dict()
+
+    def census(self):
+        tx, ty = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._L.swe_get_census(self._h, None, ctypes.byref(tx), ctypes.byref(ty)))
+        out = np.zeros((ty.value, tx.value), dtype=np.int32)
+        self._check(self._L.swe_get_census(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           ctypes.byref(tx), ctypes.byref(ty)))
+        return out
+
+    @property
+    def tile(self):
+        d = self.diag()
+        return d["tile_x"], d["tile_y"]

@@ -1,0 +1,250 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 build, per step from identical inputs: relative L-infinity <= 1e-11
+    (H against max|H|, momenta against max|H| sqrt(g max|H|), b against
+    max(max|b|, 1e-3)); dt to 1e-13; census bit-exact.
+  * FP32 build after a config's full run: relative L1 <= 1e-4 on H and b.
+  * FP32 single step at full size, sampled windows: the per-step bound derived
+    from FP32 rounding of the largest intermediate (the free surface
+    eta <= ~25 m: ulp 2e-6) times the ~10 roundings on its path: 4e-5 m on H
+    and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta.
+"""
+import math
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_2103_15196_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_15196_gb300 import swe
+    swe.load_library()
+    return swe
+
+
+def _rel_linf(g, o, H_ref):
+    gH, gU, gV, gb = g
+    oH, oU, oV, ob = o
+    hs = max(np.abs(H_ref).max(), 1e-12)
+    ms = hs * math.sqrt(9.81 * hs)
+    bs = max(np.abs(ob).max(), 1e-3)
+    return (np.abs(gH - oH).max() / hs, np.abs(gU - oU).max() / ms,
+            np.abs(gV - oV).max() / ms, np.abs(gb - ob).max() / bs)
+
+
+def _fp64_solver(gpu, sc, bw=128, th=32, **kw):
+    S = gpu.Solver(sc.nx, sc.ny, sc.dx, precision="fp64", block_cols=bw, tile_rows=th, **kw)
+    if sc.manning_block > 1:
+        S.set_manning(sc.manning, block=sc.manning_block)
+    else:
+        S.set_manning(np.broadcast_to(sc.manning, (sc.ny, sc.nx)).copy(), block=0)
+    if sc.src is not None:
+        S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
+    S.set_state(sc.H, sc.Hu, sc.Hv, sc.b)
+    return S
+
+
+def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, **kw):
+    S = _fp64_solver(gpu, sc, bw=bw, th=th, **kw)
+    d = S.diag()
+    p = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, tile_x=d["tile_x"], tile_y=d["tile_y"], **kw)
+    n_cell = sc.manning_per_cell()
+    hydro = orc.Hydrograph(sc.hydro_t, sc.hydro_Q) if sc.src is not None else None
+    st = orc.State(*S.get_state())
+    t = 0.0
+    worst = np.zeros(4)
+    for it in range(nsteps):
+        o, info = orc.step(p, st, n_cell, src=sc.src, hydro=hydro, t=t)
+        dt = S.step()
+        g = S.get_state()
+        assert dt == pytest.approx(info.dt, rel=1e-13, abs=0), it
+        err = np.array(_rel_linf(g, o.arrays(), o.H))
+        worst = np.maximum(worst, err)
+        assert np.all(err <= tol), (it, err)
+        if check_census:
+            cg = S.census()
+            co = orc.census(p, g[0], sc.src)
+            assert np.array_equal(cg, co), it
+        st = orc.State(*g)
+        t = t + info.dt
+    S.close()
+    return worst
+
+
+def test_fp64_parity_dam_break_128(gpu, orc):
+    """Config 1: 128^2 dam break over the noisy erodible bed, 500 steps."""
+    sc = I.dam_break(128, 128, seed=1)
+    worst = _per_step_parity(gpu, orc, sc, 500, bw=128, th=32)
+    print("fp64 dam break worst rel Linf (H, Hu, Hv, b):", worst)
+
+
+def test_fp64_parity_flood_channel_ragged_tiles(gpu, orc):
+    """Initially dry fractal terrain, inflow hydrograph, partially dry fronts,
+    HGS skipping on, grid not a multiple of the block (200 x 176 cells with
+    120 x 32 blocks)."""
+    sc = I.flood_channel(200, dx=5.0, seed=2, peak=300.0)
+    sc2 = I.Scenario(200, 176, 5.0, sc.H[:176], sc.Hu[:176], sc.Hv[:176], sc.b[:176],
+                     sc.manning, manning_block=64, src=sc.src[:176], hydro_t=sc.hydro_t,
+                     hydro_Q=sc.hydro_Q)
+    # start from a wetted state: run the oracle a little first to get fronts
+    p0 = orc.Params(nx=200, ny=176, dx=5.0)
+    st, t, _ = orc.run(p0, orc.State(sc2.H, sc2.Hu, sc2.Hv, sc2.b), sc2.manning_per_cell(), 150,
+                       src=sc2.src, hydro=orc.Hydrograph(sc2.hydro_t, sc2.hydro_Q))
+    sc2.H, sc2.Hu, sc2.Hv, sc2.b = st.H, st.Hu, st.Hv, st.b
+    assert (st.H > 1e-4).sum() > 20
+    worst = _per_step_parity(gpu, orc, sc2, 200, bw=128, th=32)
+    print("fp64 flood channel worst rel Linf:", worst)
+
+
+@pytest.mark.parametrize("shape", [(1, 9), (9, 1), (3, 5), (4, 4), (130, 3)])
+def test_fp64_parity_tiny_and_thin_grids(gpu, orc, shape):
+    ny, nx = shape
+    g = I.rng(31)
+    H = 1.0 + g.uniform(0, 0.5, (ny, nx))
+    Hu = g.normal(0, 0.3, (ny, nx))
+    Hv = g.normal(0, 0.3, (ny, nx))
+    b = g.uniform(-0.05, 0.05, (ny, nx))
+    sc = I.Scenario(nx, ny, 1.0, H, Hu, Hv, b, np.full((1, 1), 0.03), manning_block=256)
+    _per_step_parity(gpu, orc, sc, 20, bw=128, th=32, A_J=0.05)
+
+
+def test_fp64_advance_lands_on_t_end(gpu, orc):
+    sc = I.dam_break(64, 48, x_dam=30, seed=3)
+    S = _fp64_solver(gpu, sc, bw=128, th=16)
+    n = S.advance(2.5)
+    assert S.t == 2.5
+    g = S.get_state()
+    p = orc.Params(nx=64, ny=48, dx=1.0)
+    st, t, infos = orc.run(p, orc.State(sc.H, sc.Hu, sc.Hv, sc.b), 0.03, 10000, t_end=2.5)
+    assert t == 2.5 and len(infos) == n
+    err = _rel_linf(g, st.arrays(), st.H)
+    assert max(err) < 1e-10, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hgs_skip_is_bit_exact_on_gpu(gpu, precision):
+    """Skipping dry blocks (and not even copying blocks dry twice in a row)
+    gives bit-identical states to computing every block."""
+    sc = I.flood_channel(512, dx=5.0, seed=2, peak=500.0)
+    res = []
+    for hgs in (1, 0):
+        S = gpu.Solver(512, 512, 5.0, precision=precision, hgs_skip=hgs, tile_rows=32)
+        S.set_manning(sc.manning, block=64)
+        S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
+        S.set_state(sc.H, sc.Hu, sc.Hv, sc.b)
+        S.run_steps(400)
+        S.sync()
+        res.append((S.get_state(np.float64), S.diag()))
+        S.close()
+    (a, da), (b, db) = res
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert da["t"] == db["t"]
+    assert da["active_tiles"] < da["total_tiles"]
+    assert da["wet_cells"] > 0
+
+
+def test_fp32_flood_channel_2048_full_run(gpu):
+    """Config 2: 2048^2 FP32 state vs the FP64 oracle after 10^4 steps, at the
+    oracle's final time: relative L1 <= 1e-4 on H and b.  The oracle's final
+    state is stored by tests/golden/make_cfg2_reference.py (oracle only)."""
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "cfg2_oracle.npz"))
+    sc = I.flood_channel(2048, dx=5.0, seed=2, peak=500.0)
+    assert sc.b.sum() == pytest.approx(float(ref["b0_sum"]), rel=1e-12)
+    assert sc.manning.sum() == pytest.approx(float(ref["n_sum"]), rel=1e-12)
+    t_ref = float(ref["t"])
+    S = gpu.Solver(2048, 2048, 5.0, precision="fp32")
+    S.set_manning(sc.manning, block=64)
+    S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
+    S.set_state(sc.H, sc.Hu, sc.Hv, sc.b)
+    n_gpu = S.advance(t_ref)
+    g = S.get_state()
+    d = S.diag()
+    H_ref = ref["H"]
+    b_ref = sc.b + ref["db"]
+    relH = np.abs(g[0] - H_ref).sum() / np.abs(H_ref).sum()
+    relb = np.abs(g[3] - b_ref).sum() / np.abs(b_ref).sum()
+    db_o = ref["db"]
+    rel_db = np.abs((g[3] - sc.b) - db_o).sum() / max(np.abs(db_o).sum(), 1e-30)
+    print(f"cfg2: steps gpu {n_gpu} oracle {int(ref['steps'])} t={t_ref:.3f} relL1 H {relH:.3e} "
+          f"b {relb:.3e} bed-change {rel_db:.3e} wet {(H_ref > 1e-4).sum()} "
+          f"vol gpu {d['water_volume']:.6e} oracle {H_ref.sum() * 25.0:.6e} inflow gpu {d['inflow_volume']:.6e} "
+          f"oracle {float(ref['inflow']):.6e}")
+    assert abs(n_gpu - int(ref["steps"])) <= 2
+    assert relH <= 1e-4 and relb <= 1e-4
+    S.close()
+
+
+def test_fp32_full_size_step_sampled(gpu, orc):
+    """16384^2 half-wet fractal terrain in the benchmark's launch
+    configuration: one FP32 step, compared on sampled windows (interior,
+    corners, edges, wet/dry fronts) with the oracle evaluated window by window
+    at the oracle's own dt."""
+    n = int(os.environ.get("SWE_FULL_N", "16384"))
+    sc = I.half_wet(n, dx=5.0, seed=3)
+    S = gpu.Solver(n, n, 5.0, precision="fp32")
+    S.set_manning(sc.manning, block=64)
+    S.set_state(sc.H, sc.Hu, sc.Hv, sc.b)
+    dt_gpu = S.step()
+    g = S.get_state(np.float32)
+    S.close()
+    H = sc.H.astype(np.float64)
+    b = sc.b.astype(np.float64)
+    Z = np.zeros_like(H)
+    st = orc.State(H, Z, Z.copy(), b)
+    ncell = np.ascontiguousarray(sc.manning_per_cell(), dtype=np.float64)
+    p = orc.Params(nx=n, ny=n, dx=5.0)
+    dt_o, _ = orc.dt_from_terms(p, *orc.dt_terms(p, st, ncell))
+    assert dt_gpu == pytest.approx(dt_o, rel=1e-6)
+    rng = I.rng(99)
+    w = 24
+    wet = H > 1e-4
+    front = np.argwhere(wet[1:-1, 1:-1] != wet[2:, 1:-1])
+    picks = [(0, 0), (0, n - w), (n - w, 0), (n - w, n - w), (n // 2 - w // 2, 0), (0, n // 2 - w // 2)]
+    picks += [tuple(rng.integers(0, n - w, 2)) for _ in range(8)]
+    picks += [tuple(np.clip(front[i] - w // 2, 0, n - w)) for i in rng.integers(0, len(front), 8)]
+    worst = np.zeros(4)
+    for (y0, x0) in picks:
+        y0, x0 = int(y0), int(x0)
+        out, bad = orc.step_rect(p, st, ncell, dt_o, (x0, y0, x0 + w, y0 + w))
+        assert bad == 0
+        for q in range(4):
+            gw = g[q][y0:y0 + w, x0:x0 + w].astype(np.float64)
+            e = np.abs(gw - out[q])
+            tol = 4e-5 + (2e-5 * np.abs(out[q]) if q in (1, 2) else 0.0)
+            worst[q] = max(worst[q], e.max())
+            assert np.all(e <= tol), (q, (y0, x0), e.max())
+    print("full-size sampled worst abs err (H, Hu, Hv, b):", worst)
+
+
+def test_error_paths(gpu):
+    """Out-of-order calls, bad arguments and a host-injected NaN are reported
+    as status codes, and the handle stays usable."""
+    S = gpu.Solver(32, 32, 1.0, precision="fp32")
+    with pytest.raises(gpu.SweError) as e:
+        S.step()
+    assert e.value.status == gpu.SWE_ESTATE
+    with pytest.raises(gpu.SweError) as e:
+        S.set_manning(np.full(4, -1.0), block=16)
+    assert e.value.status == gpu.SWE_EINVAL
+    H = np.ones((32, 32))
+    H[5, 7] = np.nan
+    Z = np.zeros_like(H)
+    with pytest.raises(gpu.SweError) as e:
+        S.set_state(H, Z, Z, Z)
+        S.step()
+    assert e.value.status == gpu.SWE_ENUMERIC
+    H[5, 7] = 1.0
+    S.set_state(H, Z, Z, Z)   # a fresh state clears the status
+    S.step()
+    S.close()
