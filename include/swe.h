@@ -70,7 +70,7 @@ typedef struct {
     int dt_literal_D;    /* 1: D of Eq. 7 as printed, 0: C_J-scaled D; default 0 */
     int precision;       /* SWE_FP64 or SWE_FP32; default SWE_FP32 */
     int hgs_skip;        /* skip dry blocks (K1 rule of Sec. 3); default 1 */
-    int tile_rows;       /* rows per block strip; 0 = chosen by the library */
+    int tile_rows;       /* rows per block strip, a multiple of 8; 0 = chosen by the library */
     int block_cols;      /* threads (columns) per block, 128 or 256; 0 = auto */
     double neg_tol;      /* H' < -neg_tol => SWE_ENUMERIC; default 1e-10 (FP64), 1e-4 (FP32) */
 } swe_params;

@@ -140,7 +140,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     if (!(p.dx > 0) || !(p.g > 0) || !(p.cfl_K > 0 && p.cfl_K < 1) || !(p.eps_wet > 0) || !(p.dt_max > 0) ||
         !(p.psi >= 0 && p.psi < 1) || !(p.A_J >= 0) || !(p.m_exp >= 0) || !(p.C_J >= 0) || !(p.d50 > 0) ||
         !(p.s_rel > 1) || !(p.C_Sh >= 0) || (p.precision != SWE_FP32 && p.precision != SWE_FP64) ||
-        (p.aj_mode != 0 && p.aj_mode != 1) || p.tile_rows < 0 ||
+        (p.aj_mode != 0 && p.aj_mode != 1) || p.tile_rows < 0 || (p.tile_rows % 8) != 0 ||
         (p.block_cols != 0 && p.block_cols != 128 && p.block_cols != 256))
         return SWE_EINVAL;
     swe_handle *h = new swe_handle();

@@ -279,22 +279,317 @@ template <typename T> __device__ inline K<T> load_k(const SweConst &c, const Swe
 
 // ---------------------------------------------------------- step kernel
 
-// Shared-memory rings (each row padded by 2 entries on both sides so the
-// edge threads' out-of-block neighbour reads stay in bounds; those threads'
+// Fast even extension for row indices within one reflection of the grid;
+// falls back to the general form for grids thinner than the stencil.
+__device__ inline int reflect(int i, int n, int &sgn) {
+    if (i >= -n && i < 2 * n) {
+        sgn = 1;
+        if (i < 0) { i = -1 - i; sgn = -1; }
+        else if (i >= n) { i = 2 * n - 1 - i; sgn = -1; }
+        return i;
+    }
+    return ext_index(i, n, sgn);
+}
+
+// Precision-specific arithmetic.  FP32 (production): hardware reciprocal,
+// exp2/log2 power, a branch-free limiter and one reciprocal shared by the
+// three HLL fluxes.  FP64 (parity): IEEE division, cbrt and the oracle's
+// operation order.
+template <typename T> struct Ar;
+template <> struct Ar<double> {
+    __device__ static inline void div2(double a, double b, double d, double &x, double &y) { x = a / d; y = b / d; }
+    __device__ static inline double pow43(double x) { return x * cbrt(x); }
+    __device__ static inline double minmod(double a, double b) { return swe_impl::minmod(a, b); }
+};
+template <> struct Ar<float> {
+    __device__ static inline void div2(float a, float b, float d, float &x, float &y) {
+        const float r = 1.0f / d;
+        x = a * r; y = b * r;
+    }
+    __device__ static inline float pow43(float x) { return exp2f(1.33333333f * log2f(x)); }
+    __device__ static inline float minmod(float a, float b) {
+        const float m = fminf(fabsf(a), fabsf(b));
+        return (a * b > 0.f) ? copysignf(m, a) : 0.f;
+    }
+};
+
+// HLL fluxes of mass and both momenta sharing the bounds sL <= sR.
+template <typename T>
+__device__ inline void hll3(T HL, T HR, T uL, T uR, T wxL, T wxR, T wyL, T wyR, T sL, T sR,
+                            T &Fm, T &Fx, T &Fy) {
+    T UxL = HL * wxL, UxR = HR * wxR, UyL = HL * wyL, UyR = HR * wyR;
+    Fm = hll(HL, HR, HL * uL, HR * uR, sL, sR);
+    Fx = hll(UxL, UxR, UxL * uL, UxR * uR, sL, sR);
+    Fy = hll(UyL, UyR, UyL * uL, UyR * uR, sL, sR);
+}
+template <>
+__device__ inline void hll3<float>(float HL, float HR, float uL, float uR, float wxL, float wxR, float wyL,
+                                   float wyR, float sL, float sR, float &Fm, float &Fx, float &Fy) {
+    const float UxL = HL * wxL, UxR = HR * wxR, UyL = HL * wyL, UyR = HR * wyR;
+    const float FmL = HL * uL, FmR = HR * uR, FxL = UxL * uL, FxR = UxR * uR, FyL = UyL * uL, FyR = UyR * uR;
+    if (sL >= 0.f) { Fm = FmL; Fx = FxL; Fy = FyL; return; }
+    if (sR <= 0.f) { Fm = FmR; Fx = FxR; Fy = FyR; return; }
+    const float inv = 1.0f / (sR - sL), ss = sL * sR;
+    Fm = ((sR * FmL - sL * FmR) + ss * (HR - HL)) * inv;
+    Fx = ((sR * FxL - sL * FxR) + ss * (UxR - UxL)) * inv;
+    Fy = ((sR * FyL - sL * FyR) + ss * (UyR - UyL)) * inv;
+}
+
+// Face states of one cell along one axis from its two neighbours: limited
+// slope sigma = minmod(q - q_m, q_p - q); minus-side face value q - sigma/2,
+// plus-side face value q + sigma/2.
+template <typename T> __device__ inline void cell_faces(T qm, T q, T qp, T &lo, T &hi) {
+    const T sg = Ar<T>::minmod(q - qm, qp - q);
+    hi = q + T(0.5) * sg;
+    lo = q - T(0.5) * sg;
+}
+
+// Fluxes through a face with at least one wet cell, from reconstructed states
+// (L: H, eta, un, wx, wy of the minus cell's plus face; R: the plus cell's
+// minus face), the wet flags, the cells' normal transport velocity, Grass
+// load and bed.  (A face between two dry cells carries exactly zero flux.)
+template <typename T>
+__device__ inline void face_flux2(const SweConst &c, const K<T> &k, const T L[5], const T R[5],
+                                  bool wet_c, bool wet_e, T un_c, T un_e, T Jn_c, T Jn_e, T Ja_c, T Ja_e,
+                                  T b_c, T b_e, T &Fm, T &Fx, T &Fy, T &Fj) {
+    const T bL = L[1] - L[0], bR = R[1] - R[0];
+    const T bf = bL > bR ? bL : bR;
+    T HL = L[1] - bf, HR = R[1] - bf;
+    if (!(HL > T(0))) HL = T(0);
+    if (!(HR > T(0))) HR = T(0);
+    const T uL = L[2], uR = R[2];
+    const T cL = wet_c ? mm_sqrt(k.g * HL) : T(0);
+    const T cR = wet_e ? mm_sqrt(k.g * HR) : T(0);
+    const T aL = uL - cL, aR = uR - cR, pL = uL + cL, pR = uR + cR;
+    const T sL = aL < aR ? aL : aR, sR = pL > pR ? pL : pR;
+    hll3<T>(HL, HR, uL, uR, L[3], R[3], L[4], R[4], sL, sR, Fm, Fx, Fy);
+    Fj = T(0);
+    if (c.sediment_on) {
+        const T su = un_c + un_e;
+        const T Jadv = su > T(0) ? Jn_c : (su < T(0) ? Jn_e : T(0));
+        Fj = Jadv - (k.cjh * (Ja_c + Ja_e)) * (b_e - b_c);
+    }
+}
+
+// Per-cell terms of Eq. 7 and the census for a new state value.
+template <typename T>
+__device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T hun, T hvn, T bn, T ajn,
+                                      bool src, int &cnt, T &m0, T &m1, T &m2, unsigned &st) {
+    const bool wet = is_wet(hn, c);
+    cnt += (wet || src) ? 1 : 0;
+    if (wet) {
+        T u, v;
+        Ar<T>::div2(hun, hvn, hn, u, v);
+        const T va = mm_sqrt(u * u + v * v);
+        const T cs = va + mm_sqrt(k.g * hn);
+        m0 = va > m0 ? va : m0;
+        m1 = cs > m1 ? cs : m1;
+        T jx, jy, ja;
+        grass<T>(c, k, true, hn, ajn, u, v, jx, jy, ja);
+        m2 = ja > m2 ? ja : m2;
+    }
+    if (!(hn >= -k.neg_tol)) st |= 2u;
+    if (!mm_finite(((hn + bn) + hun) + hvn)) st |= 1u;
+}
+
+// Shared-memory rings; each row is padded by 2 entries on both sides so the
+// edge threads' out-of-block neighbour reads stay in bounds (those threads'
 // results are never used).
 template <typename T, int BW> struct StepSmem {
     static constexpr int RW = BW + 4;
-    T H[8][RW], b[8][RW], u[8][RW], v[8][RW];       // state ring (rows s-7..s)
-    T Hh[4][RW];                                    // K4 particle depth ring
-    T ux[4][RW], uy[4][RW], wx[4][RW], wy[4][RW];   // K4/K6 velocity rings
-    T jx[4][RW], jy[4][RW], ja[4][RW];              // Grass load ring
-    T F[4][RW];                                     // x-face fluxes of the update row
+    T H[8][RW], b[8][RW];                       // state rows s-7..s
+    T u[4][RW], v[4][RW];                       // cell velocities v^n, rows s-3..s
+    T Hh[4][RW];                                // K4 particle depth H^{n+1/2}
+    T ux[4][RW], uy[4][RW], wx[4][RW], wy[4][RW];  // K4 transport / K6 end velocity
+    T jx[4][RW], jy[4][RW], ja[4][RW];          // Grass load from the transport velocity
+    T qw[2][5][RW];                             // x-direction minus-face states (H, eta, ux, wx, wy)
+    T xf[2][4][RW];                             // x-face fluxes (face t|t+1): mass, x-mom, y-mom, Exner
 };
 
 template <typename T> __device__ inline T tab(const void *p, int i) { return reinterpret_cast<const T *>(p)[i]; }
 
+// The sweep of one block.  pos<P>(s) runs the pipeline at sweep position s
+// with P = s mod 8 known at compile time (so every ring slot is a constant):
+//   load row s | K4 depth, row s-1 | K2 K4 K5 K6 + Grass, row s-2 |
+//   K8 update, row s-5 | x-faces, row s-4 | per-cell limited face states,
+//   row s-3, and the y-face (s-4|s-3).
+// Every read of a neighbour column refers to a row finished at an earlier
+// position, so one __syncthreads per position suffices.
+template <typename T, int BW> struct Sweep {
+    StepSmem<T, BW> &S;
+    const SweConst &c;
+    const SweBufs &B;
+    const K<T> &k;
+    const void *in;
+    void *out;
+    int y0, y1, x, xx, mcol, o;
+    T sxT;
+    bool out_lane;
+    int gn2_row, aj_row;
+    T gn2, ajo, aj_out;
+    T qE[5], qN[5], G1[4], G2[4];
+    int cnt;
+    T m0, m1, m2;
+    unsigned st;
+    T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
+    int asy, bsy;
+
+    __device__ Sweep(StepSmem<T, BW> &S_, const SweConst &c_, const SweBufs &B_, const K<T> &k_)
+        : S(S_), c(c_), B(B_), k(k_) {}
+
+    template <int P> __device__ __forceinline__ void pos(int s) {
+        constexpr int P8 = P & 7, PM1_8 = (P + 7) & 7, PM2_8 = (P + 6) & 7, PM3_8 = (P + 5) & 7,
+                      PM4_8 = (P + 4) & 7, PM5_8 = (P + 3) & 7;
+        constexpr int P4 = P & 3, PM1_4 = (P + 3) & 3, PM2_4 = (P + 2) & 3, PM3_4 = (P + 1) & 3,
+                      PM4_4 = P & 3, PM5_4 = (P + 3) & 3;
+        constexpr int PM3_2 = (P + 1) & 1, PM4_2 = P & 1, PM5_2 = (P + 1) & 1;
+        T v_s = T(0);
+        // ---------------- load row s (ghost rows by even extension)
+        if (s >= y0 - 4 && s <= y1 + 3) {
+            const T H = aH, Hu = aHu, Hv = aHv, bb = ab;
+            const T syT = T(asy);
+            aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
+            if (s + 2 <= y1 + 3) {
+                const int yy = reflect(s + 2, c.ny, bsy);
+                CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+            }
+            const bool wet = is_wet(H, c);
+            S.H[P8][o] = H;
+            S.b[P8][o] = bb;
+            T u = T(0);
+            if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
+            S.u[P4][o] = u;
+            S.v[P4][o] = v_s;
+        }
+        // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
+        if (s - 1 >= y0 - 3 && s - 1 <= y1 + 2) {
+            const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - S.v[PM2_4][o]));
+            S.Hh[PM1_4][o] = S.H[PM1_8][o] / A;
+        }
+        // ---------------- K2, K4, K5, K6 and Grass load, row s-2
+        if (s - 2 >= y0 - 2 && s - 2 <= y1 + 1) {
+            const int r = s - 2;
+            const T Hc = S.H[PM2_8][o];
+            const bool wet = is_wet(Hc, c);
+            T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
+            if (wet) {
+                const T bc = S.b[PM2_8][o], u = S.u[PM2_4][o], v = S.v[PM2_4][o];
+                int sy;
+                const int my = reflect(r, c.ny, sy) >> c.man_shift;
+                if (my != gn2_row) {
+                    gn2_row = my;
+                    gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
+                    if (c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
+                }
+                const T HE = S.H[PM2_8][o + 1], bE = S.b[PM2_8][o + 1];
+                const T HW = S.H[PM2_8][o - 1], bW = S.b[PM2_8][o - 1];
+                const T HN = S.H[PM1_8][o], bN = S.b[PM1_8][o];
+                const T HS = S.H[PM3_8][o], bS = S.b[PM3_8][o];
+                const bool wE = is_wet(HE, c), wW = is_wet(HW, c), wN = is_wet(HN, c), wS = is_wet(HS, c);
+                // K2: forces at t_n
+                const T ec = Hc + bc;
+                const T ax = axis_force<T>(k, ec, T(1), HE + bE, bE, wE, HW + bW, bW, wW);
+                const T ay = axis_force<T>(k, ec, T(1), HN + bN, bN, wN, HS + bS, bS, wS);
+                // K4: predictor velocity, point-implicit Manning at |v^n|
+                const T cf = gn2 / Ar<T>::pow43(Hc);
+                const T va = mm_sqrt(u * u + v * v);
+                const T den = T(1) + k.hdt * (cf * va);
+                Ar<T>::div2(u + k.hdt * ax, v + k.hdt * ay, den, vtx, vty);
+                // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
+                const T hc = S.Hh[PM2_4][o], ech = hc + bc;
+                const T hE = S.Hh[PM2_4][o + 1], hW = S.Hh[PM2_4][o - 1];
+                const T hN = S.Hh[PM1_4][o], hS = S.Hh[PM3_4][o];
+                const T ratio = hc / Hc;
+                const T bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, wE, hW + bW, bW, wW);
+                const T byf = axis_force<T>(k, ech, ratio, hN + bN, bN, wN, hS + bS, bS, wS);
+                // K6: corrector (Lagrangian end) velocity, Manning at |vt|
+                const T vat = mm_sqrt(vtx * vtx + vty * vty);
+                const T den2 = T(1) + k.dt * (cf * vat);
+                Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
+                grass<T>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
+            }
+            S.ux[PM2_4][o] = vtx; S.uy[PM2_4][o] = vty; S.wx[PM2_4][o] = wxv; S.wy[PM2_4][o] = wyv;
+            S.jx[PM2_4][o] = jx; S.jy[PM2_4][o] = jy; S.ja[PM2_4][o] = ja;
+        }
+        // ---------------- K8: update row s-5
+        if (s - 5 >= y0 && s - 5 <= y1 - 1 && out_lane) {
+            const int r = s - 5;
+            const T Hc = S.H[PM5_8][o], bc = S.b[PM5_8][o];
+            bool src = false;
+            if (c.nsrc > 0)
+                for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
+            T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
+            if (src) hn = hn + k.dHs;
+            T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
+            T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
+            if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
+            const T bn = bc - k.cb * ((S.xf[PM5_2][3][o] - S.xf[PM5_2][3][o - 1]) + (G1[3] - G2[3]));
+            CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
+            if (c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
+                aj_row = r >> c.man_shift;
+                aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
+            }
+            cell_epilogue2<T>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
+        }
+        // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
+        // (from the previous position) and the minus-face state of t+1
+        if (s - 4 >= y0 && s - 4 <= y1 - 1) {
+            const bool wc = is_wet(S.H[PM4_8][o], c), we = is_wet(S.H[PM4_8][o + 1], c);
+            T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
+            if (wc || we) {
+                T R[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) R[q] = S.qw[PM4_2][q][o + 1];
+                face_flux2<T>(c, k, qE, R, wc, we, S.ux[PM4_4][o], S.ux[PM4_4][o + 1], S.jx[PM4_4][o],
+                              S.jx[PM4_4][o + 1], S.ja[PM4_4][o], S.ja[PM4_4][o + 1], S.b[PM4_8][o],
+                              S.b[PM4_8][o + 1], f0, f1, f2, f3);
+            }
+            S.xf[PM4_2][0][o] = f0; S.xf[PM4_2][1][o] = f1; S.xf[PM4_2][2][o] = f2; S.xf[PM4_2][3][o] = f3;
+        }
+        // ---------------- per-cell limited face states (K7 reconstruction), row s-3,
+        // and the y-face (s-4 | s-3)
+        if (s - 3 >= y0 - 1 && s - 3 <= y1) {
+            const T H0 = S.H[PM3_8][o], b0 = S.b[PM3_8][o];
+            const T Hm = S.H[PM3_8][o - 1], Hp = S.H[PM3_8][o + 1];
+            const T Hs = S.H[PM4_8][o], Hn = S.H[PM2_8][o];
+            const bool w0 = is_wet(H0, c), ws = is_wet(Hs, c);
+            const bool need = w0 || ws || is_wet(Hm, c) || is_wet(Hp, c) || is_wet(Hn, c);
+            T G[4] = {T(0), T(0), T(0), T(0)};
+            if (need) {
+                const T e0 = H0 + b0;
+                T lo, hi;
+                // x direction: (H, eta, ux, wx, wy) at t-1, t, t+1
+                cell_faces<T>(Hm, H0, Hp, lo, hi); S.qw[PM3_2][0][o] = lo; qE[0] = hi;
+                cell_faces<T>(Hm + S.b[PM3_8][o - 1], e0, Hp + S.b[PM3_8][o + 1], lo, hi); S.qw[PM3_2][1][o] = lo; qE[1] = hi;
+                cell_faces<T>(S.ux[PM3_4][o - 1], S.ux[PM3_4][o], S.ux[PM3_4][o + 1], lo, hi); S.qw[PM3_2][2][o] = lo; qE[2] = hi;
+                cell_faces<T>(S.wx[PM3_4][o - 1], S.wx[PM3_4][o], S.wx[PM3_4][o + 1], lo, hi); S.qw[PM3_2][3][o] = lo; qE[3] = hi;
+                cell_faces<T>(S.wy[PM3_4][o - 1], S.wy[PM3_4][o], S.wy[PM3_4][o + 1], lo, hi); S.qw[PM3_2][4][o] = lo; qE[4] = hi;
+                // y direction: (H, eta, uy, wx, wy) at rows r-1, r, r+1 (own column)
+                T qS[5], hn5[5];
+                cell_faces<T>(Hs, H0, Hn, qS[0], hn5[0]);
+                cell_faces<T>(Hs + S.b[PM4_8][o], e0, Hn + S.b[PM2_8][o], qS[1], hn5[1]);
+                cell_faces<T>(S.uy[PM4_4][o], S.uy[PM3_4][o], S.uy[PM2_4][o], qS[2], hn5[2]);
+                cell_faces<T>(S.wx[PM4_4][o], S.wx[PM3_4][o], S.wx[PM2_4][o], qS[3], hn5[3]);
+                cell_faces<T>(S.wy[PM4_4][o], S.wy[PM3_4][o], S.wy[PM2_4][o], qS[4], hn5[4]);
+                if (s - 3 >= y0 && (ws || w0))
+                    face_flux2<T>(c, k, qN, qS, ws, w0, S.uy[PM4_4][o], S.uy[PM3_4][o], S.jy[PM4_4][o],
+                                  S.jy[PM3_4][o], S.ja[PM4_4][o], S.ja[PM3_4][o], S.b[PM4_8][o], b0,
+                                  G[0], G[1], G[2], G[3]);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) qN[q] = hn5[q];
+            }
+            if (s - 3 >= y0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { G2[q] = G1[q]; G1[q] = G[q]; }
+            }
+        }
+        __syncthreads();
+    }
+};
+
+// One step, one block per (column band, row strip).
 template <typename T, int BW>
-__global__ void __launch_bounds__(BW) step_kernel(SweConst c, SweBufs B) {
+__global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     SweDev *dev = B.dev;
@@ -337,164 +632,40 @@ __global__ void __launch_bounds__(BW) step_kernel(SweConst c, SweBufs B) {
     if (t == 0) atomicAdd(&dev->cells_computed, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
 
     const K<T> k = load_k<T>(c, dev);
-    const int x = tx0 - 4 + t;                       // this thread's column
+    Sweep<T, BW> w(S, c, B, k);
+    w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
+    w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
-    const int xx = ext_index(x, c.nx, sx);
-    const T sxT = T(sx);
-    const int mrow_x = xx >> c.man_shift;
-    const bool out_lane = (t >= 4) && (t < BW - 4) && (x < c.nx);
-    const int o = t + 2;                             // padded smem index
-
-    // y-face fluxes of the previous sweep position (south face of the update row)
-    T GS0 = T(0), GS1 = T(0), GS2 = T(0), GS3 = T(0);
-    int cnt = 0;
-    T m0 = T(0), m1 = T(0), m2 = T(0);
-    unsigned st = 0;
-
-    // prefetch distance 2: a two-deep register shift (rows s and s+1)
-    T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
-    int asy, bsy;
+    w.xx = ext_index(w.x, c.nx, sx);
+    w.sxT = T(sx);
+    w.mcol = w.xx >> c.man_shift;
+    w.out_lane = (t >= 4) && (t < BW - 4) && (w.x < c.nx);
+    w.o = t + 2;                                     // padded smem index
+    w.gn2_row = -1; w.aj_row = -1;
+    w.gn2 = T(0); w.ajo = T(0); w.aj_out = T(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) { w.qE[q] = T(0); w.qN[q] = T(0); }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); }
+    w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
-        int yy = ext_index(y0 - 4, c.ny, asy);
-        CellIO<T>::load(in, (long long)yy * c.nx + xx, aH, aHu, aHv, ab);
-        yy = ext_index(y0 - 3, c.ny, bsy);
-        CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+        int yy = reflect(y0 - 4, c.ny, w.asy);
+        CellIO<T>::load(in, (long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
+        yy = reflect(y0 - 3, c.ny, w.bsy);
+        CellIO<T>::load(in, (long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
-
-    for (int s = y0 - 4; s <= y1 + 3; ++s) {
-        // ---------------- load row s (ghost rows by even extension)
-        {
-            const T H = aH, Hu = aHu, Hv = aHv, bb = ab;
-            const T syT = T(asy);
-            aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
-            if (s + 2 <= y1 + 3) {
-                int yy = ext_index(s + 2, c.ny, bsy);
-                CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
-            }
-            const bool wet = is_wet(H, c);
-            const int r8 = s & 7;
-            S.H[r8][o] = H;
-            S.b[r8][o] = bb;
-            S.u[r8][o] = wet ? (sxT * Hu) / H : T(0);
-            S.v[r8][o] = wet ? (syT * Hv) / H : T(0);
-        }
-        __syncthreads();
-        // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
-        if (s - 1 >= y0 - 3) {
-            const int r = s - 1, r8 = r & 7;
-            T A = T(1) + k.c4 * ((S.u[r8][o + 1] - S.u[r8][o - 1]) + (S.v[(r + 1) & 7][o] - S.v[(r - 1) & 7][o]));
-            S.Hh[r & 3][o] = S.H[r8][o] / A;
-        }
-        __syncthreads();
-        // ---------------- K2, K4, K5, K6 and Grass load, row s-2
-        if (s - 2 >= y0 - 2) {
-            const int r = s - 2, r8 = r & 7, rn = (r + 1) & 7, rs = (r - 1) & 7;
-            const int a4 = r & 3, an = (r + 1) & 3, as = (r - 1) & 3;
-            const T Hc = S.H[r8][o], bc = S.b[r8][o], u = S.u[r8][o], v = S.v[r8][o];
-            const bool wet = is_wet(Hc, c);
-            int sy;
-            const int yy = ext_index(r, c.ny, sy);
-            const int mi = (yy >> c.man_shift) * c.man_w + mrow_x;
-            const T gn2 = tab<T>(B.gn2, mi);
-            T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0);
-            {
-                // K2: forces at t_n
-                T ax = T(0), ay = T(0);
-                const T ec = Hc + bc;
-                if (wet) {
-                    const T HE = S.H[r8][o + 1], bE = S.b[r8][o + 1];
-                    const T HW = S.H[r8][o - 1], bW = S.b[r8][o - 1];
-                    const T HN = S.H[rn][o], bN = S.b[rn][o];
-                    const T HS = S.H[rs][o], bS = S.b[rs][o];
-                    ax = axis_force<T>(k, ec, T(1), HE + bE, bE, is_wet(HE, c), HW + bW, bW, is_wet(HW, c));
-                    ay = axis_force<T>(k, ec, T(1), HN + bN, bN, is_wet(HN, c), HS + bS, bS, is_wet(HS, c));
-                }
-                // K4: predictor velocity with point-implicit Manning at |v^n|
-                const T Hm = wet ? Hc : k.eps;
-                const T cf = gn2 / pow43(Hm);
-                const T va = mm_sqrt(u * u + v * v);
-                const T den = T(1) + k.hdt * (cf * va);
-                vtx = (u + k.hdt * ax) / den;
-                vty = (v + k.hdt * ay) / den;
-                // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
-                T bxf = T(0), byf = T(0);
-                if (wet) {
-                    const T hc = S.Hh[a4][o], ech = hc + bc;
-                    const T hE = S.Hh[a4][o + 1], bE = S.b[r8][o + 1], HE = S.H[r8][o + 1];
-                    const T hW = S.Hh[a4][o - 1], bW = S.b[r8][o - 1], HW = S.H[r8][o - 1];
-                    const T hN = S.Hh[an][o], bN = S.b[rn][o], HN = S.H[rn][o];
-                    const T hS = S.Hh[as][o], bS = S.b[rs][o], HS = S.H[rs][o];
-                    const T ratio = hc / Hc;
-                    bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, is_wet(HE, c), hW + bW, bW, is_wet(HW, c));
-                    byf = axis_force<T>(k, ech, ratio, hN + bN, bN, is_wet(HN, c), hS + bS, bS, is_wet(HS, c));
-                }
-                // K6: corrector (Lagrangian end) velocity with Manning at |vt|
-                const T vat = mm_sqrt(vtx * vtx + vty * vty);
-                const T den2 = T(1) + k.dt * (cf * vat);
-                wxv = (u + k.dt * bxf) / den2;
-                wyv = (v + k.dt * byf) / den2;
-            }
-            S.ux[a4][o] = vtx; S.uy[a4][o] = vty; S.wx[a4][o] = wxv; S.wy[a4][o] = wyv;
-            T jx, jy, ja;
-            grass<T>(c, k, wet, Hc, tab<T>(B.ajn, mi), vtx, vty, jx, jy, ja);
-            S.jx[a4][o] = jx; S.jy[a4][o] = jy; S.ja[a4][o] = ja;
-        }
-        __syncthreads();
-        // ---------------- K7: fluxes of row s-4 (x-face t|t+1) and the y-face (s-4 | s-3)
-        T GN0 = T(0), GN1 = T(0), GN2 = T(0), GN3 = T(0);
-        const bool upd = (s - 4 >= y0);
-        if (s - 3 >= y0) {
-            const int r = s - 4;
-            if (upd) {
-                const int r8 = r & 7, a4 = r & 3;
-                T Hq[4], eq[4], uq[4], wxq[4], wyq[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int oj = o - 1 + j;
-                    Hq[j] = S.H[r8][oj]; eq[j] = Hq[j] + S.b[r8][oj];
-                    uq[j] = S.ux[a4][oj]; wxq[j] = S.wx[a4][oj]; wyq[j] = S.wy[a4][oj];
-                }
-                T f0, f1, f2, f3;
-                face_flux<T>(c, k, Hq, eq, uq, wxq, wyq, is_wet(Hq[1], c), is_wet(Hq[2], c),
-                             S.jx[a4][o], S.jx[a4][o + 1], S.ja[a4][o], S.ja[a4][o + 1],
-                             S.b[r8][o], S.b[r8][o + 1], f0, f1, f2, f3);
-                S.F[0][o] = f0; S.F[1][o] = f1; S.F[2][o] = f2; S.F[3][o] = f3;
-            }
-            // y-face between rows r and r+1 of this column
-            T Hq[4], eq[4], uq[4], wxq[4], wyq[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int rr = r - 1 + j;
-                Hq[j] = S.H[rr & 7][o]; eq[j] = Hq[j] + S.b[rr & 7][o];
-                uq[j] = S.uy[rr & 3][o]; wxq[j] = S.wx[rr & 3][o]; wyq[j] = S.wy[rr & 3][o];
-            }
-            face_flux<T>(c, k, Hq, eq, uq, wxq, wyq, is_wet(Hq[1], c), is_wet(Hq[2], c),
-                         S.jy[r & 3][o], S.jy[(r + 1) & 3][o], S.ja[r & 3][o], S.ja[(r + 1) & 3][o],
-                         S.b[r & 7][o], S.b[(r + 1) & 7][o], GN0, GN1, GN2, GN3);
-        }
-        __syncthreads();
-        // ---------------- K8: update row s-4
-        if (upd) {
-            const int r = s - 4, r8 = r & 7, a4 = r & 3;
-            if (out_lane) {
-                const T Hc = S.H[r8][o], bc = S.b[r8][o];
-                bool src = false;
-                for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
-                T hn = Hc - k.dtdx * ((S.F[0][o] - S.F[0][o - 1]) + (GN0 - GS0));
-                if (src) hn = hn + k.dHs;
-                T hun = Hc * S.wx[a4][o] - k.dtdx * ((S.F[1][o] - S.F[1][o - 1]) + (GN1 - GS1));
-                T hvn = Hc * S.wy[a4][o] - k.dtdx * ((S.F[2][o] - S.F[2][o - 1]) + (GN2 - GS2));
-                if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
-                const T bn = bc - k.cb * ((S.F[3][o] - S.F[3][o - 1]) + (GN3 - GS3));
-                const long long kk = (long long)r * c.nx + x;
-                CellIO<T>::store(out, kk, hn, hun, hvn, bn);
-                const int mi = (r >> c.man_shift) * c.man_w + mrow_x;
-                cell_epilogue<T>(c, k, hn, hun, hvn, bn, tab<T>(B.ajn, mi), src, cnt, m0, m1, m2, st);
-            }
-        }
-        GS0 = GN0; GS1 = GN1; GS2 = GN2; GS3 = GN3;
+    // sweep positions y0-8 .. y1+4 in groups of 8 (y0 is a multiple of 8)
+    for (int s = y0 - 8; s <= y1 + 4; s += 8) {
+        w.template pos<0>(s);
+        w.template pos<1>(s + 1);
+        w.template pos<2>(s + 2);
+        w.template pos<3>(s + 3);
+        w.template pos<4>(s + 4);
+        w.template pos<5>(s + 5);
+        w.template pos<6>(s + 6);
+        w.template pos<7>(s + 7);
     }
-    block_finish<T, BW>(cnt, m0, m1, m2, st, tile, cen_out, dev, 1);
+    block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state

@@ -77,15 +77,20 @@ def fractal_dem(nx: int, ny: int, seed: int, beta: float = 2.0, relief: float = 
     """Spectral-synthesis fractal surface with power spectrum ~ |k|^-beta,
     rescaled to `relief` metres (min 0)."""
     g = rng(seed)
-    ky = np.fft.fftfreq(ny).astype(np.float32)[:, None]
-    kx = np.fft.rfftfreq(nx).astype(np.float32)[None, :]
+    # float64 spectra up to 4096^2 (the result rounded to float32 is then the
+    # same on every platform to the last bit, practically); float32 above that
+    # to bound host memory
+    wide = nx * ny <= 4096 * 4096
+    ft = np.float64 if wide else np.float32
+    ky = np.fft.fftfreq(ny).astype(ft)[:, None]
+    kx = np.fft.rfftfreq(nx).astype(ft)[None, :]
     kk = np.sqrt(kx * kx + ky * ky)
     kk[0, 0] = 1.0
-    amp = kk ** np.float32(-beta / 2.0)
+    amp = kk ** ft(-beta / 2.0)
     amp[0, 0] = 0.0
     del kk
-    phase = g.uniform(0.0, 2.0 * np.pi, size=amp.shape).astype(np.float32)
-    spec = (amp * np.exp(1j * phase)).astype(np.complex64)
+    phase = g.uniform(0.0, 2.0 * np.pi, size=amp.shape).astype(ft)
+    spec = (amp * np.exp(1j * phase)).astype(np.complex128 if wide else np.complex64)
     del amp, phase
     try:
         import scipy.fft as sfft
@@ -93,11 +98,12 @@ def fractal_dem(nx: int, ny: int, seed: int, beta: float = 2.0, relief: float = 
     except Exception:  # pragma: no cover - numpy fallback
         z = np.fft.irfft2(spec, s=(ny, nx))
     del spec
-    z = np.asarray(z, dtype=np.float32)
+    z = np.asarray(z, dtype=ft)
     lo, hi = float(z.min()), float(z.max())
     z -= lo
-    z *= np.float32(relief / (hi - lo))
-    return z.astype(dtype, copy=False)
+    z *= ft(relief / (hi - lo))
+    # quantise to float32 so both sides of a comparison see the same terrain
+    return z.astype(np.float32).astype(dtype, copy=False)
 
 
 def carve_channel(b: np.ndarray, dx: float, width_m: float = 40.0, depth_m: float = 2.0,
