@@ -25,6 +25,7 @@ UNITS = {
     "swe_f32.cu": ["--use_fast_math"],
     "swe_f64.cu": ["--fmad=false"],
     "swe_capi.cu": [],
+    "swe_noalloc.cu": [],
 }
 
 
