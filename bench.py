@@ -223,7 +223,8 @@ def run_ours(args):
     n, K, W = args.size, args.steps, args.warmup
     sc = make_workload(n)
     stream = torch.cuda.Stream()
-    S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=0 if args.hgs_off else 1)
+    S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=0 if args.hgs_off else 1,
+                   tile_rows=args.tile_rows, block_cols=args.block_cols)
     S.set_manning(sc.manning, block=64)
     H32 = [np.ascontiguousarray(a, dtype=np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)]
     S.set_state(*H32)
@@ -336,6 +337,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=16384)
     ap.add_argument("--hgs-off", action="store_true")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per block strip (0: library default)")
+    ap.add_argument("--block-cols", type=int, default=0, help="threads per block, 128 or 256 (0: default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

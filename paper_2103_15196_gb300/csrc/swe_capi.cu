@@ -158,7 +158,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     long long ncell = (long long)p.nx * p.ny;
     h->bw = p.block_cols ? p.block_cols : (p.nx <= 120 ? 128 : 256);
     int th = p.tile_rows;
-    if (th == 0) th = ncell >= (1ll << 26) ? 128 : (ncell >= (1ll << 22) ? 64 : 32);
+    if (th == 0) th = ncell >= (1ll << 26) ? 256 : (ncell >= (1ll << 22) ? 64 : 32);
     SweConst &c = h->c;
     c.nx = p.nx; c.ny = p.ny;
     c.tw = h->bw - 8; c.th = th;
@@ -177,6 +177,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     c.A_J = p.A_J; c.m_exp = p.m_exp; c.sm1 = p.s_rel - 1.0; c.d50 = p.d50; c.C_J = p.C_J;
     c.psi = p.psi; c.K = p.cfl_K; c.dt_max = p.dt_max; c.neg_tol = h->p.neg_tol;
     c.eps_f = float_floor_of(p.eps_wet);
+    swe_fill_f32(c);
 
     SweBufs &b = h->b;
     size_t ntiles = (size_t)c.tiles_x * c.tiles_y;

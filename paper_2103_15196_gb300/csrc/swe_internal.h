@@ -40,7 +40,15 @@ struct SweConst {
     int nsrc;               // number of source cells
     double g, dx, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, C_J, psi, K, dt_max, neg_tol;
     float eps_f;            // largest float <= eps: (float)H > eps_f <=> (double)H > eps
+    struct { float g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol; } f;  // the same, rounded to FP32
 };
+
+// Fills the FP32 copies of the model constants.
+inline void swe_fill_f32(SweConst &c) {
+    c.f.g = (float)c.g; c.f.eps = (float)c.eps; c.f.coef = (float)c.coef; c.f.cjh = (float)c.cjh;
+    c.f.ksh = (float)c.ksh; c.f.A_J = (float)c.A_J; c.f.m_exp = (float)c.m_exp; c.f.sm1 = (float)c.sm1;
+    c.f.d50 = (float)c.d50; c.f.neg_tol = (float)c.neg_tol;
+}
 
 // Device pointers of one solver instance.
 struct SweBufs {

@@ -268,12 +268,22 @@ __device__ inline void cell_epilogue(const SweConst &c, const K<T> &k, T hn, T h
     if (!mm_finite(hn) || !mm_finite(bn) || !mm_finite(hun) || !mm_finite(hvn)) st |= 1u;
 }
 
-template <typename T> __device__ inline K<T> load_k(const SweConst &c, const SweDev *dev) {
-    K<T> k;
-    k.g = T(c.g); k.eps = T(c.eps); k.coef = T(c.coef); k.cjh = T(c.cjh); k.ksh = T(c.ksh);
-    k.A_J = T(c.A_J); k.m_exp = T(c.m_exp); k.sm1 = T(c.sm1); k.d50 = T(c.d50); k.neg_tol = T(c.neg_tol);
-    k.dt = T(dev->dt); k.dtdx = T(dev->dtdx); k.hdt = T(dev->hdt); k.c4 = T(dev->c4); k.cb = T(dev->cb);
-    k.dHs = T(dev->dHs);
+template <typename T> __device__ inline K<T> load_k(const SweConst &c, const SweDev *dev);
+template <> __device__ inline K<double> load_k<double>(const SweConst &c, const SweDev *dev) {
+    K<double> k;
+    k.g = c.g; k.eps = c.eps; k.coef = c.coef; k.cjh = c.cjh; k.ksh = c.ksh;
+    k.A_J = c.A_J; k.m_exp = c.m_exp; k.sm1 = c.sm1; k.d50 = c.d50; k.neg_tol = c.neg_tol;
+    k.dt = dev->dt; k.dtdx = dev->dtdx; k.hdt = dev->hdt; k.c4 = dev->c4; k.cb = dev->cb; k.dHs = dev->dHs;
+    return k;
+}
+// FP32: the model constants come pre-rounded in the kernel parameters (so
+// they can stay in the constant bank); the per-step ones from the bookkeeping.
+template <> __device__ inline K<float> load_k<float>(const SweConst &c, const SweDev *dev) {
+    K<float> k;
+    k.g = c.f.g; k.eps = c.f.eps; k.coef = c.f.coef; k.cjh = c.f.cjh; k.ksh = c.f.ksh;
+    k.A_J = c.f.A_J; k.m_exp = c.f.m_exp; k.sm1 = c.f.sm1; k.d50 = c.f.d50; k.neg_tol = c.f.neg_tol;
+    k.dt = (float)dev->dt; k.dtdx = (float)dev->dtdx; k.hdt = (float)dev->hdt; k.c4 = (float)dev->c4;
+    k.cb = (float)dev->cb; k.dHs = (float)dev->dHs;
     return k;
 }
 
@@ -433,13 +443,29 @@ template <typename T, int BW> struct Sweep {
     unsigned st;
     T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
     int asy, bsy;
+    T *Hc, *Hp, *bc, *bp;   // current / previous 4-row banks of the 8-row H and b rings
+
+    // Row s-D of the 8-row ring, for a sweep position s = 4m + P: rows of the
+    // current group of four live in bank (m & 1), older ones in the other bank
+    // (rows s-8..s-5 of group m-2 share the current bank's slots).
+    template <int P, int D> __device__ __forceinline__ T *Hr() const {
+        constexpr int d = P - D;
+        return ((d < 0 && d >= -4) ? Hp : Hc) + (d & 3) * StepSmem<T, BW>::RW;
+    }
+    template <int P, int D> __device__ __forceinline__ T *Br() const {
+        constexpr int d = P - D;
+        return ((d < 0 && d >= -4) ? bp : bc) + (d & 3) * StepSmem<T, BW>::RW;
+    }
+    __device__ __forceinline__ void set_banks(int s) {
+        const int g = (s >> 2) & 1;
+        Hc = &S.H[4 * g][0]; Hp = &S.H[4 * (g ^ 1)][0];
+        bc = &S.b[4 * g][0]; bp = &S.b[4 * (g ^ 1)][0];
+    }
 
     __device__ Sweep(StepSmem<T, BW> &S_, const SweConst &c_, const SweBufs &B_, const K<T> &k_)
         : S(S_), c(c_), B(B_), k(k_) {}
 
     template <int P> __device__ __forceinline__ void pos(int s) {
-        constexpr int P8 = P & 7, PM1_8 = (P + 7) & 7, PM2_8 = (P + 6) & 7, PM3_8 = (P + 5) & 7,
-                      PM4_8 = (P + 4) & 7, PM5_8 = (P + 3) & 7;
         constexpr int P4 = P & 3, PM1_4 = (P + 3) & 3, PM2_4 = (P + 2) & 3, PM3_4 = (P + 1) & 3,
                       PM4_4 = P & 3, PM5_4 = (P + 3) & 3;
         constexpr int PM3_2 = (P + 1) & 1, PM4_2 = P & 1, PM5_2 = (P + 1) & 1;
@@ -454,8 +480,8 @@ template <typename T, int BW> struct Sweep {
                 CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
             const bool wet = is_wet(H, c);
-            S.H[P8][o] = H;
-            S.b[P8][o] = bb;
+            Hr<P, 0>()[o] = H;
+            Br<P, 0>()[o] = bb;
             T u = T(0);
             if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
             S.u[P4][o] = u;
@@ -464,16 +490,16 @@ template <typename T, int BW> struct Sweep {
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
         if (s - 1 >= y0 - 3 && s - 1 <= y1 + 2) {
             const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - S.v[PM2_4][o]));
-            S.Hh[PM1_4][o] = S.H[PM1_8][o] / A;
+            S.Hh[PM1_4][o] = Hr<P, 1>()[o] / A;
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
         if (s - 2 >= y0 - 2 && s - 2 <= y1 + 1) {
             const int r = s - 2;
-            const T Hc = S.H[PM2_8][o];
+            const T Hc = Hr<P, 2>()[o];
             const bool wet = is_wet(Hc, c);
             T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
             if (wet) {
-                const T bc = S.b[PM2_8][o], u = S.u[PM2_4][o], v = S.v[PM2_4][o];
+                const T bc = Br<P, 2>()[o], u = S.u[PM2_4][o], v = S.v[PM2_4][o];
                 int sy;
                 const int my = reflect(r, c.ny, sy) >> c.man_shift;
                 if (my != gn2_row) {
@@ -481,10 +507,10 @@ template <typename T, int BW> struct Sweep {
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
                     if (c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
                 }
-                const T HE = S.H[PM2_8][o + 1], bE = S.b[PM2_8][o + 1];
-                const T HW = S.H[PM2_8][o - 1], bW = S.b[PM2_8][o - 1];
-                const T HN = S.H[PM1_8][o], bN = S.b[PM1_8][o];
-                const T HS = S.H[PM3_8][o], bS = S.b[PM3_8][o];
+                const T HE = Hr<P, 2>()[o + 1], bE = Br<P, 2>()[o + 1];
+                const T HW = Hr<P, 2>()[o - 1], bW = Br<P, 2>()[o - 1];
+                const T HN = Hr<P, 1>()[o], bN = Br<P, 1>()[o];
+                const T HS = Hr<P, 3>()[o], bS = Br<P, 3>()[o];
                 const bool wE = is_wet(HE, c), wW = is_wet(HW, c), wN = is_wet(HN, c), wS = is_wet(HS, c);
                 // K2: forces at t_n
                 const T ec = Hc + bc;
@@ -514,7 +540,7 @@ template <typename T, int BW> struct Sweep {
         // ---------------- K8: update row s-5
         if (s - 5 >= y0 && s - 5 <= y1 - 1 && out_lane) {
             const int r = s - 5;
-            const T Hc = S.H[PM5_8][o], bc = S.b[PM5_8][o];
+            const T Hc = Hr<P, 5>()[o], bc = Br<P, 5>()[o];
             bool src = false;
             if (c.nsrc > 0)
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
@@ -534,24 +560,24 @@ template <typename T, int BW> struct Sweep {
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
         if (s - 4 >= y0 && s - 4 <= y1 - 1) {
-            const bool wc = is_wet(S.H[PM4_8][o], c), we = is_wet(S.H[PM4_8][o + 1], c);
+            const bool wc = is_wet(Hr<P, 4>()[o], c), we = is_wet(Hr<P, 4>()[o + 1], c);
             T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
             if (wc || we) {
                 T R[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) R[q] = S.qw[PM4_2][q][o + 1];
                 face_flux2<T>(c, k, qE, R, wc, we, S.ux[PM4_4][o], S.ux[PM4_4][o + 1], S.jx[PM4_4][o],
-                              S.jx[PM4_4][o + 1], S.ja[PM4_4][o], S.ja[PM4_4][o + 1], S.b[PM4_8][o],
-                              S.b[PM4_8][o + 1], f0, f1, f2, f3);
+                              S.jx[PM4_4][o + 1], S.ja[PM4_4][o], S.ja[PM4_4][o + 1], Br<P, 4>()[o],
+                              Br<P, 4>()[o + 1], f0, f1, f2, f3);
             }
             S.xf[PM4_2][0][o] = f0; S.xf[PM4_2][1][o] = f1; S.xf[PM4_2][2][o] = f2; S.xf[PM4_2][3][o] = f3;
         }
         // ---------------- per-cell limited face states (K7 reconstruction), row s-3,
         // and the y-face (s-4 | s-3)
         if (s - 3 >= y0 - 1 && s - 3 <= y1) {
-            const T H0 = S.H[PM3_8][o], b0 = S.b[PM3_8][o];
-            const T Hm = S.H[PM3_8][o - 1], Hp = S.H[PM3_8][o + 1];
-            const T Hs = S.H[PM4_8][o], Hn = S.H[PM2_8][o];
+            const T H0 = Hr<P, 3>()[o], b0 = Br<P, 3>()[o];
+            const T Hm = Hr<P, 3>()[o - 1], Hp = Hr<P, 3>()[o + 1];
+            const T Hs = Hr<P, 4>()[o], Hn = Hr<P, 2>()[o];
             const bool w0 = is_wet(H0, c), ws = is_wet(Hs, c);
             const bool need = w0 || ws || is_wet(Hm, c) || is_wet(Hp, c) || is_wet(Hn, c);
             T G[4] = {T(0), T(0), T(0), T(0)};
@@ -560,20 +586,20 @@ template <typename T, int BW> struct Sweep {
                 T lo, hi;
                 // x direction: (H, eta, ux, wx, wy) at t-1, t, t+1
                 cell_faces<T>(Hm, H0, Hp, lo, hi); S.qw[PM3_2][0][o] = lo; qE[0] = hi;
-                cell_faces<T>(Hm + S.b[PM3_8][o - 1], e0, Hp + S.b[PM3_8][o + 1], lo, hi); S.qw[PM3_2][1][o] = lo; qE[1] = hi;
+                cell_faces<T>(Hm + Br<P, 3>()[o - 1], e0, Hp + Br<P, 3>()[o + 1], lo, hi); S.qw[PM3_2][1][o] = lo; qE[1] = hi;
                 cell_faces<T>(S.ux[PM3_4][o - 1], S.ux[PM3_4][o], S.ux[PM3_4][o + 1], lo, hi); S.qw[PM3_2][2][o] = lo; qE[2] = hi;
                 cell_faces<T>(S.wx[PM3_4][o - 1], S.wx[PM3_4][o], S.wx[PM3_4][o + 1], lo, hi); S.qw[PM3_2][3][o] = lo; qE[3] = hi;
                 cell_faces<T>(S.wy[PM3_4][o - 1], S.wy[PM3_4][o], S.wy[PM3_4][o + 1], lo, hi); S.qw[PM3_2][4][o] = lo; qE[4] = hi;
                 // y direction: (H, eta, uy, wx, wy) at rows r-1, r, r+1 (own column)
                 T qS[5], hn5[5];
                 cell_faces<T>(Hs, H0, Hn, qS[0], hn5[0]);
-                cell_faces<T>(Hs + S.b[PM4_8][o], e0, Hn + S.b[PM2_8][o], qS[1], hn5[1]);
+                cell_faces<T>(Hs + Br<P, 4>()[o], e0, Hn + Br<P, 2>()[o], qS[1], hn5[1]);
                 cell_faces<T>(S.uy[PM4_4][o], S.uy[PM3_4][o], S.uy[PM2_4][o], qS[2], hn5[2]);
                 cell_faces<T>(S.wx[PM4_4][o], S.wx[PM3_4][o], S.wx[PM2_4][o], qS[3], hn5[3]);
                 cell_faces<T>(S.wy[PM4_4][o], S.wy[PM3_4][o], S.wy[PM2_4][o], qS[4], hn5[4]);
                 if (s - 3 >= y0 && (ws || w0))
                     face_flux2<T>(c, k, qN, qS, ws, w0, S.uy[PM4_4][o], S.uy[PM3_4][o], S.jy[PM4_4][o],
-                                  S.jy[PM3_4][o], S.ja[PM4_4][o], S.ja[PM3_4][o], S.b[PM4_8][o], b0,
+                                  S.jy[PM3_4][o], S.ja[PM4_4][o], S.ja[PM3_4][o], Br<P, 4>()[o], b0,
                                   G[0], G[1], G[2], G[3]);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) qN[q] = hn5[q];
@@ -654,16 +680,13 @@ __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
         yy = reflect(y0 - 3, c.ny, w.bsy);
         CellIO<T>::load(in, (long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
-    // sweep positions y0-8 .. y1+4 in groups of 8 (y0 is a multiple of 8)
-    for (int s = y0 - 8; s <= y1 + 4; s += 8) {
+    // sweep positions y0-8 .. y1+4 in groups of 4 (y0 is a multiple of 8)
+    for (int s = y0 - 8; s <= y1 + 4; s += 4) {
+        w.set_banks(s);
         w.template pos<0>(s);
         w.template pos<1>(s + 1);
         w.template pos<2>(s + 2);
         w.template pos<3>(s + 3);
-        w.template pos<4>(s + 4);
-        w.template pos<5>(s + 5);
-        w.template pos<6>(s + 6);
-        w.template pos<7>(s + 7);
     }
     block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
 }

@@ -108,6 +108,7 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     c.psi = p.psi; c.K = p.cfl_K; c.dt_max = p.dt_max;
     c.neg_tol = p.neg_tol >= 0 ? p.neg_tol : 1e-4;
     c.eps_f = float_floor(p.eps_wet);
+    swe_fill_f32(c);
 
     // carve the scratch: bookkeeping | census x2 | skip flags | source rows | Manning tables
     const size_t ntiles = (size_t)c.tiles_x * c.tiles_y;
