@@ -192,6 +192,44 @@ swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, int *tiles_
 swe_status swe_step_noalloc(const swe_params *p, double manning_n, const void *state_in,
                             void *state_out, void *cuda_stream, double *dt_taken);
 
+/* ---------------------------------------------------------------------
+ * Batched ensembles: independent scenarios (grids of uneven sizes and
+ * parameters, each with its own dt and time) advanced together by one
+ * persistent launch per swe_ensemble_run call, captured in a CUDA graph.
+ * Each step of each scenario is exactly the single-grid step above (same
+ * kernels, bit-identical results).  Not in the paper: the paper runs one
+ * scenario per GPU (Sec. 3); batching keeps a GB300 busy with many small
+ * grids. */
+typedef struct swe_ensemble swe_ensemble;
+
+/* n scenarios, params[k] for scenario k (all SWE_FP32, same block_cols and
+ * tile_rows; 0 = library defaults).  Each scenario is a solver handle created
+ * on the ensemble's stream (NULL: a private stream). */
+swe_status swe_ensemble_create(int n, const swe_params *params, void *cuda_stream, swe_ensemble **out);
+swe_status swe_ensemble_destroy(swe_ensemble *e);
+
+/* The handle of scenario k, for swe_set_state / swe_set_manning /
+ * swe_set_sources / swe_get_state / swe_get_diag (owned by the ensemble). */
+swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member);
+
+/* Advances every scenario by nsteps steps of its own Eq. 7 dt (no t_end clip)
+ * in one persistent cooperative launch.  Every scenario's state must be set.
+ * SWE_ETIMEOUT if the launch's grid barrier gave up (see set_timeout). */
+swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
+
+/* Times each candidate block shape (128 or 256 columns x 16..128 rows) for
+ * trial_steps steps on the current states, keeps the fastest, and restores
+ * the states and times (step counters and inflow totals restart).  Outputs
+ * (nullable) the chosen shape. */
+swe_status swe_ensemble_autotune(swe_ensemble *e, int trial_steps, int *block_cols, int *tile_rows);
+
+/* Time limit of the persistent launch's grid barrier (default 2 s), after
+ * which every block stops and swe_ensemble_run returns SWE_ETIMEOUT with the
+ * context still usable.  extra_arrivals > 0 makes the barrier wait for that
+ * many blocks that do not exist: a test hook that exercises the time limit
+ * (the scenarios' states are then undefined).  Use 0 otherwise. */
+swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, int extra_arrivals);
+
 /* One-line description of the last error on the handle ("" if none). */
 const char *swe_last_error(const swe_handle *h);
 

@@ -26,6 +26,7 @@ UNITS = {
     "swe_f64.cu": ["--fmad=false"],
     "swe_capi.cu": [],
     "swe_noalloc.cu": [],
+    "swe_ensemble.cu": ["--use_fast_math"],
 }
 
 

@@ -54,7 +54,7 @@ struct swe_handle {
     double *h_diag = nullptr;     // pinned read-back of the diagnostics sums
     double *d_diag = nullptr;
     int diag_blocks = 0;
-    void *allocs[16] = {};
+    void *allocs[32] = {};
     int nalloc = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
@@ -77,7 +77,7 @@ static bool is_f32(const swe_handle *h) { return h->p.precision == SWE_FP32; }
 
 static cudaError_t dev_alloc(swe_handle *h, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-    if (e == cudaSuccess && h->nalloc < 16) h->allocs[h->nalloc++] = *p;
+    if (e == cudaSuccess && h->nalloc < 32) h->allocs[h->nalloc++] = *p;
     return e;
 }
 
@@ -570,3 +570,49 @@ extern "C" swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, 
 }
 
 extern "C" const char *swe_last_error(const swe_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+// ---------------------------------------------------------------- internal hooks
+
+namespace swe_impl {
+bool handle_view(swe_handle *h, SweConst **c, SweBufs **b, cudaStream_t *s, int *bw, int *precision, bool *state_set) {
+    if (!h) return false;
+    if (c) *c = &h->c;
+    if (b) *b = &h->b;
+    if (s) *s = h->stream;
+    if (bw) *bw = h->bw;
+    if (precision) *precision = h->p.precision;
+    if (state_set) *state_set = h->state_set;
+    return true;
+}
+
+int handle_free_stepping(swe_handle *h) { return (int)free_stepping(h); }
+
+int handle_retile(swe_handle *h, int bw, int th) {
+    if (!h || (bw != 128 && bw != 256) || th < 8 || (th % 8) != 0) return SWE_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SWE_ECUDA;
+    SweConst &c = h->c;
+    const int tw = bw - 8;
+    const int tx = (c.nx + tw - 1) / tw, ty = (c.ny + th - 1) / th;
+    const size_t nt = (size_t)tx * ty;
+    void *cen0 = nullptr, *cen1 = nullptr, *skp = nullptr;
+    if (dev_alloc(h, &cen0, nt * sizeof(int)) != cudaSuccess || dev_alloc(h, &cen1, nt * sizeof(int)) != cudaSuccess ||
+        dev_alloc(h, &skp, nt) != cudaSuccess) {
+        dev_free(h, cen0); dev_free(h, cen1); dev_free(h, skp);
+        return SWE_ENOMEM;
+    }
+    dev_free(h, h->b.census[0]); dev_free(h, h->b.census[1]); dev_free(h, h->b.skipped);
+    h->b.census[0] = (int *)cen0; h->b.census[1] = (int *)cen1; h->b.skipped = (unsigned char *)skp;
+    h->bw = bw;
+    c.tw = tw; c.th = th; c.tiles_x = tx; c.tiles_y = ty;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    if (!h->state_set) return SWE_OK;
+    // census of the current state (its buffer is buf[n & 1]); the maxima the
+    // census kernel gathers are those of the same state, so dt is unchanged
+    if (read_dev(h) != SWE_OK) return SWE_ECUDA;
+    if (L_init(h) != cudaSuccess) return SWE_ECUDA;
+    // the init kernel restarted the accumulation: re-take the maxima
+    if (L_between(h, 2) != cudaSuccess) return SWE_ECUDA;
+    return (int)read_dev(h);
+}
+}  // namespace swe_impl
+

@@ -1,0 +1,395 @@
+// Batched ensembles of independent flood scenarios (grids of uneven sizes and
+// parameters) advanced together by ONE persistent launch per run call,
+// captured in a CUDA graph.
+//
+// Each scenario is an ordinary solver handle (swe_create): its state, Manning
+// field, sources and diagnostics are set and read with the usual calls.  The
+// persistent kernel walks a flattened list of (scenario, block) work items:
+//   for each step: every block takes work items round-robin and runs the
+//   same per-block step as the single-grid kernel (K1 skip, K2-K8, census and
+//   Eq. 7 maxima); grid barrier; one thread per scenario forms that
+//   scenario's next dt (its own K3; scenarios keep their own time); barrier.
+// The grid barrier spins with a time limit: if it runs out the kernel sets a
+// status bit and returns, so the host reads SWE_ETIMEOUT and the context stays
+// usable.  The cooperative launch guarantees all blocks are co-resident.
+//
+// An autotuner (swe_ensemble_autotune) times each candidate block shape on
+// the ensemble's own states and keeps the fastest.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "swe_kernels.cuh"
+
+using namespace swe_impl;
+
+namespace swe_impl {
+
+struct EnsScen {
+    SweConst c;
+    SweBufs B;
+};
+
+__device__ inline unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-counting grid barrier over `expected` blocks with a time limit.
+// bar[0] counts arrivals, bar[1] is the generation.  Returns false (and sets
+// the timeout status bit) if the other blocks did not arrive in time.
+__device__ bool grid_sync(unsigned *bar, unsigned expected, unsigned long long timeout_ns, unsigned *status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == expected - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicOr(status, SWE_STATUS_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned *)status & SWE_STATUS_TIMEOUT) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int BW>
+__global__ void __launch_bounds__(BW, 2)
+ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restrict__ items, int nitems,
+                int nsteps, unsigned *bar, unsigned expected, unsigned *status, unsigned long long timeout_ns) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
+    for (int step = 0; step < nsteps; ++step) {
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const int4 w = items[it];
+            __syncthreads();
+            step_tile<float, BW, true>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
+        }
+        if (!grid_sync(bar, expected, timeout_ns, status)) return;
+        if (blockIdx.x == 0)
+            for (int k = threadIdx.x; k < nscen; k += BW) between_body<float>(scen[k].c, scen[k].B, 1);
+        if (!grid_sync(bar, expected, timeout_ns, status)) return;
+    }
+}
+
+}  // namespace swe_impl
+
+struct swe_ensemble {
+    std::vector<swe_handle *> members;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int bw = 256, th = 64;
+    EnsScen *d_scen = nullptr;
+    int4 *d_items = nullptr;
+    size_t items_cap = 0;
+    unsigned *d_bar = nullptr;   // [0] arrivals, [1] generation, [2] status
+    unsigned long long timeout_ns = 2000000000ull;
+    int extra_arrivals = 0;
+    std::map<long long, cudaGraphExec_t> graphs;
+    int nitems = 0;
+    int grid = 0;            // co-resident blocks of the persistent kernel for bw
+    bool graph_ok = true;    // false if this driver cannot capture the cooperative launch
+};
+
+namespace {
+
+template <int BW> int resident_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = sizeof(StepSmem<float, BW>);
+    cudaFuncSetAttribute(ensemble_kernel<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_kernel<BW>, BW, smem);
+    return std::max(1, per) * sms;
+}
+
+void clear_graphs(swe_ensemble *e) {
+    for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
+    e->graphs.clear();
+    e->grid = 0;
+}
+
+// Uploads the scenario descriptors and the work list (scenario, bx, by).
+swe_status upload(swe_ensemble *e) {
+    const int n = (int)e->members.size();
+    std::vector<EnsScen> sc(n);
+    std::vector<int4> items;
+    for (int k = 0; k < n; ++k) {
+        SweConst *c = nullptr;
+        SweBufs *b = nullptr;
+        bool set = false;
+        handle_view(e->members[k], &c, &b, nullptr, nullptr, nullptr, &set);
+        if (!set) return SWE_ESTATE;
+        if (handle_free_stepping(e->members[k]) != SWE_OK) return SWE_ECUDA;
+        sc[k].c = *c;
+        sc[k].B = *b;
+        for (int by = 0; by < c->tiles_y; ++by)
+            for (int bx = 0; bx < c->tiles_x; ++bx) items.push_back(make_int4(k, bx, by, 0));
+    }
+    if (items.size() > e->items_cap) {
+        cudaFree(e->d_items);
+        e->d_items = nullptr;
+        if (cudaMalloc(&e->d_items, items.size() * sizeof(int4)) != cudaSuccess) return SWE_ENOMEM;
+        e->items_cap = items.size();
+        clear_graphs(e);   // captured launches point at the old list
+    }
+    if ((int)items.size() != e->nitems) clear_graphs(e);
+    e->nitems = (int)items.size();
+    if (cudaMemcpyAsync(e->d_scen, sc.data(), n * sizeof(EnsScen), cudaMemcpyHostToDevice, e->stream) != cudaSuccess ||
+        cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, e->stream) !=
+            cudaSuccess)
+        return SWE_ECUDA;
+    return SWE_OK;
+}
+
+template <int BW> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
+    const int grid = e->grid;
+    const size_t smem = sizeof(StepSmem<float, BW>);
+    cudaError_t err = cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned), e->stream);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BW);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = e->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const EnsScen *sc = e->d_scen;
+    const int4 *it = e->d_items;
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW>, sc, (int)e->members.size(), it, e->nitems, nsteps,
+                              e->d_bar, (unsigned)(grid + e->extra_arrivals), e->d_bar + 2, e->timeout_ns);
+}
+
+cudaError_t launch_any(swe_ensemble *e, int nsteps) {
+    return e->bw == 128 ? launch_persistent<128>(e, nsteps) : launch_persistent<256>(e, nsteps);
+}
+
+// The graph of one persistent launch of `nsteps` steps (cached per count).
+swe_status graph_for(swe_ensemble *e, int nsteps, cudaGraphExec_t *out) {
+    auto f = e->graphs.find(nsteps);
+    if (f != e->graphs.end()) { *out = f->second; return SWE_OK; }
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SWE_ECUDA;
+    cudaError_t le = launch_any(e, nsteps);
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        cudaGetLastError();
+        e->graph_ok = false;   // run the same single persistent launch without a graph
+        return SWE_ECUDA;
+    }
+    cudaGraphExec_t ge;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return SWE_ECUDA;
+    e->graphs[nsteps] = ge;
+    *out = ge;
+    return SWE_OK;
+}
+
+swe_status check(swe_ensemble *e) {
+    unsigned st = 0;
+    if (cudaMemcpyAsync(&st, e->d_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, e->stream) != cudaSuccess ||
+        cudaStreamSynchronize(e->stream) != cudaSuccess)
+        return SWE_ECUDA;
+    if (st & SWE_STATUS_TIMEOUT) {
+        // clear the bit so the ensemble can be used again once the cause is fixed
+        cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream);
+        cudaStreamSynchronize(e->stream);
+        return SWE_ETIMEOUT;
+    }
+    for (swe_handle *h : e->members) {
+        swe_status s = swe_sync(h);
+        if (s != SWE_OK) return s;
+    }
+    return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void *cuda_stream, swe_ensemble **out) {
+    if (n < 1 || !params || !out) return SWE_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k)
+        if (params[k].precision != SWE_FP32 || params[k].block_cols != params[0].block_cols ||
+            params[k].tile_rows != params[0].tile_rows)
+            return SWE_EINVAL;
+    swe_ensemble *e = new swe_ensemble();
+    if (cuda_stream) {
+        e->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) { delete e; return SWE_ECUDA; }
+        e->own_stream = true;
+    }
+    e->bw = params[0].block_cols ? params[0].block_cols : 256;
+    e->th = params[0].tile_rows ? params[0].tile_rows : 64;
+    for (int k = 0; k < n; ++k) {
+        swe_params p = params[k];
+        p.block_cols = e->bw;
+        p.tile_rows = e->th;
+        swe_handle *h = nullptr;
+        swe_status s = swe_create(&p, e->stream, &h);
+        if (s != SWE_OK) { swe_ensemble_destroy(e); return s; }
+        e->members.push_back(h);
+    }
+    if (cudaMalloc(&e->d_scen, n * sizeof(EnsScen)) != cudaSuccess ||
+        cudaMalloc(&e->d_bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream) != cudaSuccess) {
+        swe_ensemble_destroy(e);
+        return SWE_ENOMEM;
+    }
+    *out = e;
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_ensemble_destroy(swe_ensemble *e) {
+    if (!e) return SWE_OK;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    clear_graphs(e);
+    for (swe_handle *h : e->members) swe_destroy(h);
+    cudaFree(e->d_scen);
+    cudaFree(e->d_items);
+    cudaFree(e->d_bar);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    delete e;
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member) {
+    if (!e || !member || k < 0 || k >= (int)e->members.size()) return SWE_EINVAL;
+    *member = e->members[k];
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
+    if (!e || nsteps < 0) return SWE_EINVAL;
+    if (nsteps == 0) return SWE_OK;
+    swe_status s = upload(e);
+    if (s != SWE_OK) return s;
+    if (e->grid == 0) e->grid = e->bw == 128 ? resident_blocks<128>() : resident_blocks<256>();
+    // one persistent launch per call (split only beyond 2^30 steps)
+    while (nsteps > 0) {
+        const int chunk = (int)std::min<int64_t>(nsteps, 1 << 30);
+        cudaGraphExec_t g;
+        if (e->graph_ok && graph_for(e, chunk, &g) == SWE_OK) {
+            if (cudaGraphLaunch(g, e->stream) != cudaSuccess) return SWE_ECUDA;
+        } else {
+            if (launch_any(e, chunk) != cudaSuccess) return SWE_ECUDA;
+        }
+        nsteps -= chunk;
+    }
+    return check(e);
+}
+
+extern "C" swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, int extra_arrivals) {
+    if (!e || !(seconds > 0) || extra_arrivals < 0) return SWE_EINVAL;
+    e->timeout_ns = (unsigned long long)(seconds * 1e9);
+    e->extra_arrivals = extra_arrivals;
+    clear_graphs(e);
+    if (cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream) != cudaSuccess) return SWE_ECUDA;
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_ensemble_autotune(swe_ensemble *e, int trial_steps, int *block_cols, int *tile_rows) {
+    if (!e || trial_steps < 1) return SWE_EINVAL;
+    const int n = (int)e->members.size();
+    // save every member's state (device copies) and time
+    std::vector<std::vector<float>> saved;
+    std::vector<double> times(n);
+    std::vector<void *> tmp(n, nullptr);
+    for (int k = 0; k < n; ++k) {
+        SweConst *c;
+        bool set;
+        handle_view(e->members[k], &c, nullptr, nullptr, nullptr, nullptr, &set);
+        if (!set) return SWE_ESTATE;
+        const size_t N = (size_t)c->nx * c->ny;
+        if (cudaMalloc(&tmp[k], 4 * N * sizeof(float)) != cudaSuccess) {
+            for (void *p : tmp) cudaFree(p);
+            return SWE_ENOMEM;
+        }
+        float *f = (float *)tmp[k];
+        swe_status s = swe_get_state_ex(e->members[k], f, f + N, f + 2 * N, f + 3 * N, SWE_FP32, SWE_DEVICE);
+        if (s == SWE_OK) s = swe_get_time(e->members[k], &times[k]);
+        if (s != SWE_OK) { for (void *p : tmp) cudaFree(p); return s; }
+    }
+    auto restore = [&]() -> swe_status {
+        for (int k = 0; k < n; ++k) {
+            SweConst *c;
+            handle_view(e->members[k], &c, nullptr, nullptr, nullptr, nullptr, nullptr);
+            const size_t N = (size_t)c->nx * c->ny;
+            const float *f = (const float *)tmp[k];
+            swe_status s = swe_set_state_ex(e->members[k], f, f + N, f + 2 * N, f + 3 * N, SWE_FP32, SWE_DEVICE);
+            if (s == SWE_OK) s = swe_set_time(e->members[k], times[k]);
+            if (s != SWE_OK) return s;
+        }
+        return SWE_OK;
+    };
+    const int cand_bw[2] = {128, 256};
+    const int cand_th[4] = {16, 32, 64, 128};
+    float best = INFINITY;
+    int best_bw = e->bw, best_th = e->th;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    swe_status s = SWE_OK;
+    for (int bw : cand_bw)
+        for (int th : cand_th) {
+            e->bw = bw;
+            e->th = th;
+            for (swe_handle *h : e->members)
+                if ((s = (swe_status)handle_retile(h, bw, th)) != SWE_OK) goto done;
+            clear_graphs(e);
+            if ((s = restore()) != SWE_OK) goto done;
+            // one untimed run builds the graph and warms up; then the timed run
+            if ((s = swe_ensemble_run(e, 1)) != SWE_OK) goto done;
+            if ((s = restore()) != SWE_OK) goto done;
+            if ((s = upload(e)) != SWE_OK) goto done;
+            {
+                cudaGraphExec_t g;
+                const bool use_graph = e->graph_ok && graph_for(e, trial_steps, &g) == SWE_OK;
+                cudaEventRecord(e0, e->stream);
+                if (use_graph) cudaGraphLaunch(g, e->stream);
+                else launch_any(e, trial_steps);
+                cudaEventRecord(e1, e->stream);
+                if ((s = check(e)) != SWE_OK) goto done;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_bw = bw; best_th = th; }
+            }
+        }
+    e->bw = best_bw;
+    e->th = best_th;
+    for (swe_handle *h : e->members)
+        if ((s = (swe_status)handle_retile(h, best_bw, best_th)) != SWE_OK) goto done;
+    clear_graphs(e);
+    s = restore();
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (void *p : tmp) cudaFree(p);
+    if (block_cols) *block_cols = e->bw;
+    if (tile_rows) *tile_rows = e->th;
+    return s;
+}

@@ -78,3 +78,17 @@ template <typename T> cudaError_t launch_convert_out(const SweConst &c, const vo
                                                      void *Hv, void *bb, int dst_is_f64, cudaStream_t s);
 template <typename T> cudaError_t launch_bed_source(const SweConst &c, const SweBufs &b, cudaStream_t s);
 }  // namespace swe_impl
+
+// Internal hooks of the C-ABI handle used by the ensemble (swe_ensemble.cu).
+struct swe_handle;
+namespace swe_impl {
+bool handle_view(swe_handle *h, SweConst **c, SweBufs **b, cudaStream_t *s, int *bw, int *precision, bool *state_set);
+// Changes the HGS block shape (bw threads, th rows), recomputing the census
+// of the current state; the state and time are untouched.
+int handle_retile(swe_handle *h, int bw, int th);
+// Re-prepares dt without an advance clip (after swe_advance) if needed.
+int handle_free_stepping(swe_handle *h);
+}  // namespace swe_impl
+
+#define SWE_STATUS_TIMEOUT 4u   // device status bit: a bounded grid barrier gave up
+

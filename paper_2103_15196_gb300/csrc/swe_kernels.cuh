@@ -46,6 +46,14 @@ template <> struct CellIO<float> {
         float4 c = __ldg(reinterpret_cast<const float4 *>(base) + k);
         H = c.x; Hu = c.y; Hv = c.z; b = c.w;
     }
+    // L2-coherent load, for data other blocks of the same launch rewrite
+    __device__ static inline void load_cg(const void *base, long long k, float &H, float &Hu, float &Hv, float &b) {
+        float4 c = __ldcg(reinterpret_cast<const float4 *>(base) + k);
+        H = c.x; Hu = c.y; Hv = c.z; b = c.w;
+    }
+    __device__ static inline void copy_cg(const void *src, void *dst, long long k) {
+        reinterpret_cast<float4 *>(dst)[k] = __ldcg(reinterpret_cast<const float4 *>(src) + k);
+    }
     __device__ static inline void store(void *base, long long k, float H, float Hu, float Hv, float b) {
         reinterpret_cast<float4 *>(base)[k] = make_float4(H, Hu, Hv, b);
     }
@@ -58,6 +66,17 @@ template <> struct CellIO<double> {
         const double2 *p = reinterpret_cast<const double2 *>(base) + 2 * k;
         double2 a = __ldg(p), c = __ldg(p + 1);
         H = a.x; Hu = a.y; Hv = c.x; b = c.y;
+    }
+    __device__ static inline void load_cg(const void *base, long long k, double &H, double &Hu, double &Hv, double &b) {
+        const double2 *p = reinterpret_cast<const double2 *>(base) + 2 * k;
+        double2 a = __ldcg(p), c = __ldcg(p + 1);
+        H = a.x; Hu = a.y; Hv = c.x; b = c.y;
+    }
+    __device__ static inline void copy_cg(const void *src, void *dst, long long k) {
+        const double2 *s = reinterpret_cast<const double2 *>(src) + 2 * k;
+        double2 *d = reinterpret_cast<double2 *>(dst) + 2 * k;
+        d[0] = __ldcg(s);
+        d[1] = __ldcg(s + 1);
     }
     __device__ static inline void store(void *base, long long k, double H, double Hu, double Hv, double b) {
         double2 *p = reinterpret_cast<double2 *>(base) + 2 * k;
@@ -268,22 +287,38 @@ __device__ inline void cell_epilogue(const SweConst &c, const K<T> &k, T hn, T h
     if (!mm_finite(hn) || !mm_finite(bn) || !mm_finite(hun) || !mm_finite(hvn)) st |= 1u;
 }
 
-template <typename T> __device__ inline K<T> load_k(const SweConst &c, const SweDev *dev);
-template <> __device__ inline K<double> load_k<double>(const SweConst &c, const SweDev *dev) {
+// Per-step coefficients; coherent = read through L2 (volatile), for a
+// persistent launch whose other blocks rewrote them.
+struct StepCoef { double dt, dtdx, hdt, c4, cb, dHs; };
+__device__ inline StepCoef step_coef(const SweDev *dev, bool coherent) {
+    StepCoef r;
+    if (coherent) {
+        const volatile SweDev *v = dev;
+        r.dt = v->dt; r.dtdx = v->dtdx; r.hdt = v->hdt; r.c4 = v->c4; r.cb = v->cb; r.dHs = v->dHs;
+    } else {
+        r.dt = dev->dt; r.dtdx = dev->dtdx; r.hdt = dev->hdt; r.c4 = dev->c4; r.cb = dev->cb; r.dHs = dev->dHs;
+    }
+    return r;
+}
+
+template <typename T> __device__ inline K<T> load_k(const SweConst &c, const SweDev *dev, bool coherent = false);
+template <> __device__ inline K<double> load_k<double>(const SweConst &c, const SweDev *dev, bool coherent) {
     K<double> k;
     k.g = c.g; k.eps = c.eps; k.coef = c.coef; k.cjh = c.cjh; k.ksh = c.ksh;
     k.A_J = c.A_J; k.m_exp = c.m_exp; k.sm1 = c.sm1; k.d50 = c.d50; k.neg_tol = c.neg_tol;
-    k.dt = dev->dt; k.dtdx = dev->dtdx; k.hdt = dev->hdt; k.c4 = dev->c4; k.cb = dev->cb; k.dHs = dev->dHs;
+    const StepCoef r = step_coef(dev, coherent);
+    k.dt = r.dt; k.dtdx = r.dtdx; k.hdt = r.hdt; k.c4 = r.c4; k.cb = r.cb; k.dHs = r.dHs;
     return k;
 }
 // FP32: the model constants come pre-rounded in the kernel parameters (so
 // they can stay in the constant bank); the per-step ones from the bookkeeping.
-template <> __device__ inline K<float> load_k<float>(const SweConst &c, const SweDev *dev) {
+template <> __device__ inline K<float> load_k<float>(const SweConst &c, const SweDev *dev, bool coherent) {
     K<float> k;
     k.g = c.f.g; k.eps = c.f.eps; k.coef = c.f.coef; k.cjh = c.f.cjh; k.ksh = c.f.ksh;
     k.A_J = c.f.A_J; k.m_exp = c.f.m_exp; k.sm1 = c.f.sm1; k.d50 = c.f.d50; k.neg_tol = c.f.neg_tol;
-    k.dt = (float)dev->dt; k.dtdx = (float)dev->dtdx; k.hdt = (float)dev->hdt; k.c4 = (float)dev->c4;
-    k.cb = (float)dev->cb; k.dHs = (float)dev->dHs;
+    const StepCoef r = step_coef(dev, coherent);
+    k.dt = (float)r.dt; k.dtdx = (float)r.dtdx; k.hdt = (float)r.hdt; k.c4 = (float)r.c4;
+    k.cb = (float)r.cb; k.dHs = (float)r.dHs;
     return k;
 }
 
@@ -425,7 +460,7 @@ template <typename T> __device__ inline T tab(const void *p, int i) { return rei
 //   row s-3, and the y-face (s-4|s-3).
 // Every read of a neighbour column refers to a row finished at an earlier
 // position, so one __syncthreads per position suffices.
-template <typename T, int BW> struct Sweep {
+template <typename T, int BW, bool COHERENT> struct Sweep {
     StepSmem<T, BW> &S;
     const SweConst &c;
     const SweBufs &B;
@@ -465,6 +500,11 @@ template <typename T, int BW> struct Sweep {
     __device__ Sweep(StepSmem<T, BW> &S_, const SweConst &c_, const SweBufs &B_, const K<T> &k_)
         : S(S_), c(c_), B(B_), k(k_) {}
 
+    __device__ __forceinline__ void load_cell(long long kk, T &H, T &Hu, T &Hv, T &b) const {
+        if (COHERENT) CellIO<T>::load_cg(in, kk, H, Hu, Hv, b);
+        else CellIO<T>::load(in, kk, H, Hu, Hv, b);
+    }
+
     template <int P> __device__ __forceinline__ void pos(int s) {
         constexpr int P4 = P & 3, PM1_4 = (P + 3) & 3, PM2_4 = (P + 2) & 3, PM3_4 = (P + 1) & 3,
                       PM4_4 = P & 3, PM5_4 = (P + 3) & 3;
@@ -477,7 +517,7 @@ template <typename T, int BW> struct Sweep {
             aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
             if (s + 2 <= y1 + 3) {
                 const int yy = reflect(s + 2, c.ny, bsy);
-                CellIO<T>::load(in, (long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+                load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
             const bool wet = is_wet(H, c);
             Hr<P, 0>()[o] = H;
@@ -613,17 +653,17 @@ template <typename T, int BW> struct Sweep {
     }
 };
 
-// One step, one block per (column band, row strip).
-template <typename T, int BW>
-__global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
+// One step of one block (column band bx, row strip by).  COHERENT selects
+// L2-coherent reads of the state, census and bookkeeping, needed when other
+// blocks of the same (persistent) launch rewrote them since its start.
+template <typename T, int BW, bool COHERENT>
+__device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, int bx, int by, StepSmem<T, BW> &S) {
     SweDev *dev = B.dev;
-    if (!dev->scheduled) return;
+    const volatile SweDev *vdev = dev;
+    if (!(COHERENT ? vdev->scheduled : dev->scheduled)) return;
     const int t = threadIdx.x;
-    const int bx = blockIdx.x, by = blockIdx.y;
     const int tile = by * c.tiles_x + bx;
-    const long long n = dev->n;
+    const long long n = COHERENT ? vdev->n : dev->n;
     const int par = (int)(n & 1);
     const void *in = par ? B.buf[1] : B.buf[0];
     void *out = par ? B.buf[0] : B.buf[1];
@@ -637,13 +677,17 @@ __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     if (c.hgs) {
         int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
         int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
-        bool active = cen_in[tile] > 0 || cen_in[by * c.tiles_x + l] > 0 || cen_in[by * c.tiles_x + r] > 0 ||
-                      cen_in[d * c.tiles_x + bx] > 0 || cen_in[u * c.tiles_x + bx] > 0;
+        auto cen = [&](int i) { return COHERENT ? __ldcg(cen_in + i) : cen_in[i]; };
+        bool active = cen(tile) > 0 || cen(by * c.tiles_x + l) > 0 || cen(by * c.tiles_x + r) > 0 ||
+                      cen(d * c.tiles_x + bx) > 0 || cen(u * c.tiles_x + bx) > 0;
         if (!active) {
             if (!B.skipped[tile]) {
                 int x1 = min(tx0 + c.tw, c.nx);
                 for (int y = y0; y < y1; ++y)
-                    for (int x = tx0 + t; x < x1; x += BW) CellIO<T>::copy(in, out, (long long)y * c.nx + x);
+                    for (int x = tx0 + t; x < x1; x += BW) {
+                        if (COHERENT) CellIO<T>::copy_cg(in, out, (long long)y * c.nx + x);
+                        else CellIO<T>::copy(in, out, (long long)y * c.nx + x);
+                    }
             }
             if (t == 0) {
                 if (!B.skipped[tile])
@@ -657,8 +701,8 @@ __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     }
     if (t == 0) atomicAdd(&dev->cells_computed, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
 
-    const K<T> k = load_k<T>(c, dev);
-    Sweep<T, BW> w(S, c, B, k);
+    const K<T> k = load_k<T>(c, COHERENT ? const_cast<const SweDev *>(dev) : dev, COHERENT);
+    Sweep<T, BW, COHERENT> w(S, c, B, k);
     w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
     w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
@@ -676,9 +720,9 @@ __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
         int yy = reflect(y0 - 4, c.ny, w.asy);
-        CellIO<T>::load(in, (long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
+        w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
         yy = reflect(y0 - 3, c.ny, w.bsy);
-        CellIO<T>::load(in, (long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
+        w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
     // sweep positions y0-8 .. y1+4 in groups of 4 (y0 is a multiple of 8)
     for (int s = y0 - 8; s <= y1 + 4; s += 4) {
@@ -689,6 +733,14 @@ __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
         w.template pos<3>(s + 3);
     }
     block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
+}
+
+// One step: one block per (column band, row strip).
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
+    step_tile<T, BW, false>(c, B, blockIdx.x, blockIdx.y, S);
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state
@@ -748,61 +800,71 @@ template <typename T> __device__ inline double acc_value(unsigned long long bits
 template <> __device__ inline double acc_value<float>(unsigned long long bits) { return (double)__uint_as_float((unsigned)bits); }
 template <> __device__ inline double acc_value<double>(unsigned long long bits) { return __longlong_as_double((long long)bits); }
 
+template <typename T> __device__ inline double acc_value_v(const volatile unsigned long long *p) {
+    return acc_value<T>(*p);
+}
+
 // One thread.  mode 1 (commit) first commits the step that just ran, if one
 // was scheduled (n += 1, t += dt, the maxima gathered by its epilogue become
 // the current ones); mode 2 (init) takes the maxima the census kernel
 // gathered for a freshly set state; mode 0 only re-prepares.  It then forms
 // dt of the next step from Eq. 7 (FP64), clipped to t_end - t, the source
-// increment and the step coefficients.
+// increment and the step coefficients.  The bookkeeping is accessed through
+// a volatile pointer, so the body also runs inside a persistent launch.
 template <typename T>
-__global__ void between_kernel(SweConst c, SweBufs B, int mode) {
-    SweDev *d = B.dev;
+__device__ void between_body(const SweConst &c, const SweBufs &B, int mode) {
+    volatile SweDev *d = B.dev;
     const int nsrc = c.nsrc;
     bool take = mode == 2;
     if (mode == 1 && d->scheduled) {
-        d->n += 1;
+        d->n = d->n + 1;
         d->t = d->binding == 4 ? d->t_end : d->t + d->dt;  // a clipped step lands on t_end
         d->dt_last = d->dt;
         d->binding_last = d->binding;
-        d->inflow_total += d->dHs * ((double)nsrc * (c.dx * c.dx));
+        d->inflow_total = d->inflow_total + d->dHs * ((double)nsrc * (c.dx * c.dx));
         d->active_last = d->active_tiles;
         take = true;
     }
     if (take) {
-        d->vp = acc_value<T>(d->acc[0]);
-        d->vs = acc_value<T>(d->acc[1]);
-        d->jm = acc_value<T>(d->acc[2]);
+        d->vp = acc_value_v<T>(&d->acc[0]);
+        d->vs = acc_value_v<T>(&d->acc[1]);
+        d->jm = acc_value_v<T>(&d->acc[2]);
         d->acc[0] = 0ull; d->acc[1] = 0ull; d->acc[2] = 0ull;
     }
     const double h = c.dx;
     double best = INFINITY;
     int which = 3;
-    if (d->vp > 0.0) { double a = h / (2.0 * d->vp); if (a < best) { best = a; which = 0; } }
-    if (d->vs > 0.0) { double a = h / d->vs; if (a < best) { best = a; which = 1; } }
-    if (c.sediment_on && d->jm > 0.0) {
-        double D = (c.literal_D ? d->jm : c.C_J * d->jm) / (1.0 - c.psi);
+    const double vp = d->vp, vs = d->vs, jm = d->jm, t = d->t, t_end = d->t_end;
+    if (vp > 0.0) { double a = h / (2.0 * vp); if (a < best) { best = a; which = 0; } }
+    if (vs > 0.0) { double a = h / vs; if (a < best) { best = a; which = 1; } }
+    if (c.sediment_on && jm > 0.0) {
+        double D = (c.literal_D ? jm : c.C_J * jm) / (1.0 - c.psi);
         double a = (h * h) / (2.0 * D);
         if (a < best) { best = a; which = 2; }
     }
     double dt = c.K * best;
     if (!(dt < c.dt_max)) { dt = c.dt_max; which = 3; }
     d->dt_unclipped = dt;
-    if (d->t_end < INFINITY) {
-        double rem = d->t_end - d->t;
+    if (t_end < INFINITY) {
+        double rem = t_end - t;
         if (!(rem > 0.0)) { dt = 0.0; d->done = 1; }
         else if (rem < dt) { dt = rem; which = 4; }
     }
     d->dt = dt;
     d->binding = which;
     d->scheduled = dt > 0.0 ? 1 : 0;
-    double vol = (nsrc > 0 && dt > 0.0) ? hydro_integral(c.nk, B.hyd_t, B.hyd_q, d->t, d->t + dt) : 0.0;
+    double vol = (nsrc > 0 && dt > 0.0) ? hydro_integral(c.nk, B.hyd_t, B.hyd_q, t, t + dt) : 0.0;
     d->dHs = nsrc > 0 ? vol / ((double)nsrc * (c.dx * c.dx)) : 0.0;
-    d->dtdx = dt / c.dx;
+    const double dtdx = dt / c.dx;
+    d->dtdx = dtdx;
     d->hdt = 0.5 * dt;
     d->c4 = dt / (4.0 * c.dx);
-    d->cb = d->dtdx / (1.0 - c.psi);
+    d->cb = dtdx / (1.0 - c.psi);
     d->active_tiles = 0;
 }
+
+template <typename T>
+__global__ void between_kernel(SweConst c, SweBufs B, int mode) { between_body<T>(c, B, mode); }
 
 // b += dt q / (1 - psi) on the freshly written buffer (Eq. 1 bed source).
 template <typename T>

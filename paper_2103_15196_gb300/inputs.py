@@ -194,3 +194,24 @@ def ensemble_specs(n_scen: int = 64, seed: int = 4, side_lo: int = 256, side_hi:
     return [dict(side=int(sides[k]), seed=int(1000 + k), manning=float(g.uniform(0.02, 0.06)),
                  peak=float(g.uniform(50.0, 1000.0)), d50_scale=float(g.uniform(0.5, 2.0)))
             for k in range(n_scen)]
+
+
+def ensemble_scenario(side: int, seed: int, manning: float, peak: float, d50_scale: float,
+                      dx: float = 5.0, wet_fraction: float = 0.5) -> Scenario:
+    """One member of a flood ensemble: fractal terrain with a carved channel,
+    filled half wet with a dam-break step, plus an inflow hydrograph of the
+    given peak on the channel head; uniform Manning n.  The grain-size scale
+    multiplies d50 (returned as the attribute d50)."""
+    sc = half_wet(side, dx=dx, seed=seed, wet_fraction=wet_fraction, dtype=np.float64)
+    b = sc.b
+    wc = max(1, int(round(40.0 / dx)))
+    yc = side / 2
+    rows = np.clip(np.round(yc - wc / 2).astype(np.int64), 0, side - wc) + np.arange(wc)
+    src = np.zeros((side, side), dtype=np.uint8)
+    src[rows, 0] = 1
+    ht, hq = triangular_hydrograph(peak)
+    out = Scenario(side, side, dx, sc.H, sc.Hu, sc.Hv, b, np.full((1, 1), manning), manning_block=1 << 14,
+                   src=src, hydro_t=ht, hydro_Q=hq, name=f"ensemble_{side}_{seed}")
+    out.d50 = 5e-4 * d50_scale
+    return out
+

@@ -100,6 +100,14 @@ def load_library(build_if_missing: bool = True):
         "swe_get_census": [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
+    sig.update({
+        "swe_ensemble_create": [ctypes.c_int, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
+        "swe_ensemble_destroy": [vp],
+        "swe_ensemble_member": [vp, ctypes.c_int, ctypes.POINTER(H)],
+        "swe_ensemble_run": [vp, ctypes.c_int64],
+        "swe_ensemble_autotune": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "swe_ensemble_set_timeout": [vp, ctypes.c_double, ctypes.c_int],
+    })
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -124,9 +132,22 @@ class Solver:
     precision: 'fp32' (FP32 state, FP64 dt/accumulators) or 'fp64'.
     Other keyword arguments override fields of ``swe_params``."""
 
+    @classmethod
+    def _view(cls, handle, params, precision="fp32"):
+        """A non-owning view of a handle owned elsewhere (an ensemble member)."""
+        self = cls.__new__(cls)
+        self._L = load_library()
+        self.params = params
+        self.nx, self.ny, self.dx = params.nx, params.ny, params.dx
+        self.precision = precision
+        self._h = handle
+        self._owned = False
+        return self
+
     def __init__(self, nx, ny, dx, precision="fp32", stream=None, **kw):
         L = load_library()
         self._L = L
+        self._owned = True
         p = Params()
         self._check(L.swe_params_default(ctypes.byref(p), nx, ny, dx), None)
         p.precision = SWE_FP32 if precision == "fp32" else SWE_FP64
@@ -150,7 +171,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._L.swe_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._L.swe_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -259,3 +281,67 @@ class Solver:
     def tile(self):
         d = self.diag()
         return d["tile_x"], d["tile_y"]
+
+
+class Ensemble:
+    """Independent scenarios advanced together by one persistent launch per
+    run call (swe_ensemble_* in include/swe.h).  specs: list of dicts with
+    nx, ny, dx and optional swe_params fields."""
+
+    def __init__(self, specs, stream=None, block_cols=0, tile_rows=0):
+        L = load_library()
+        self._L = L
+        n = len(specs)
+        arr = (Params * n)()
+        for k, sp in enumerate(specs):
+            p = arr[k]
+            st = L.swe_params_default(ctypes.byref(p), sp["nx"], sp["ny"], sp["dx"])
+            if st != SWE_OK:
+                raise SweError(st, "swe_params_default")
+            p.precision = SWE_FP32
+            p.block_cols = block_cols
+            p.tile_rows = tile_rows
+            for key, v in sp.items():
+                if key in ("nx", "ny", "dx"):
+                    continue
+                setattr(p, key, v)
+        h = ctypes.c_void_p()
+        st = L.swe_ensemble_create(n, arr, ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if st != SWE_OK:
+            raise SweError(st, "swe_ensemble_create failed")
+        self._h = h
+        self._params = arr
+        self.members = []
+        for k in range(n):
+            mh = ctypes.c_void_p()
+            self._check(L.swe_ensemble_member(self._h, k, ctypes.byref(mh)))
+            self.members.append(Solver._view(mh, arr[k]))
+
+    def _check(self, st):
+        if st != SWE_OK:
+            raise SweError(st, "ensemble call failed")
+
+    def run(self, nsteps):
+        self._check(self._L.swe_ensemble_run(self._h, int(nsteps)))
+
+    def autotune(self, trial_steps=5):
+        bw, th = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._L.swe_ensemble_autotune(self._h, int(trial_steps), ctypes.byref(bw), ctypes.byref(th)))
+        return bw.value, th.value
+
+    def set_timeout(self, seconds, extra_arrivals=0):
+        self._check(self._L.swe_ensemble_set_timeout(self._h, float(seconds), int(extra_arrivals)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            self._L.swe_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
