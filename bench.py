@@ -61,9 +61,9 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _profile_traffic(n):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to this grid; None if absent or taken on other kernel source."""
+def _profile_kv():
+    """Key: value lines of the committed ncu summary of the step kernel, or {}
+    if absent or taken on other kernel source."""
     path = os.path.join(ROOT, "profiles", "step_kernel_fp32_traffic.txt")
     try:
         kv = {}
@@ -71,12 +71,19 @@ def _profile_traffic(n):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_hash") != _kernel_hash():
-            return None
-        per_cell = float(kv["dram_bytes_per_cell"])
-        return per_cell * n * n
+        return kv if kv.get("kernel_source_hash") == _kernel_hash() else {}
     except Exception:
-        return None
+        return {}
+
+
+def _profile_traffic(n):
+    """DRAM bytes per launch of the step kernel (ncu), scaled to this grid."""
+    kv = _profile_kv()
+    return float(kv["dram_bytes_per_cell"]) * n * n if "dram_bytes_per_cell" in kv else None
+
+
+# GB300 instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction x 32 lanes per clock
+ISSUE_LANES_PER_CLOCK = 152 * 4 * 32
 
 
 class Clocks:
@@ -130,6 +137,21 @@ class Clocks:
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+
+def _issue_object(gcell_s, clocks):
+    """What bounds the step kernel: thread-instructions per cell (ncu, same
+    kernel source) times the measured cell rate, against the issue peak at
+    the sampled SM clock."""
+    kv = _profile_kv()
+    if "thread_inst_per_cell" not in kv:
+        return None
+    ipc = float(kv["thread_inst_per_cell"])
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = ISSUE_LANES_PER_CLOCK * mhz * 1e6 / 1e12
+    ach = gcell_s * 1e9 * ipc / 1e12
+    return {"bound": "instruction issue", "thread_inst_per_cell": ipc, "achieved": ach, "peak": peak,
+            "unit": "Tinst/s", "frac": ach / peak}
 
 
 def make_workload(n, seed=3):
@@ -372,6 +394,7 @@ def run_ours(args):
                      "kernel": "step_kernel<float,256>",
                      "algorithmic_bytes_per_launch": alg_bytes_launch,
                      "note": "launch duration = timed region / K (includes the one-thread dt kernel)"},
+        "issue": _issue_object(value, clk.summary()),
         "hgs": {"active_cell_fraction": comp / (float(n) * n * K), "copied_cell_fraction": copied / (float(n) * n * K),
                 "all_cell_equiv_GBps": BYTES_PER_CELL * n * n / (ms * 1e-3 / K) / 1e9,
                 "wet_cells_end": dd["wet_cells"], "t_end": dd["t"]},
