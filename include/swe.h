@@ -230,6 +230,73 @@ swe_status swe_ensemble_autotune(swe_ensemble *e, int trial_steps, int *block_co
  * (the scenarios' states are then undefined).  Use 0 otherwise. */
 swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, int extra_arrivals);
 
+/* ---------------------------------------------------------------------
+ * Tensor-core self-test (no counterpart in the paper): checks, on the
+ * current device, the BF16 x BF16 -> FP32 tcgen05 MMA path that the bed
+ * surrogate's convolution kernels use.  C[128][n] = A[128][k] * B[n][k]^T;
+ * A and B are BF16 bit patterns (row-major host arrays), C is FP32 (host).
+ * n = 16 or 32, k a multiple of 16 in 16..256.  SWE_ETIMEOUT if the MMA did
+ * not complete within its bounded wait. */
+swe_status swe_nn_tc_selftest(int n, int k, const uint16_t *A, const uint16_t *B, float *C);
+
+/* Turns the Exner coupling (Eq. 1-5) on or off for the following steps and
+ * re-forms dt (Eq. 7) for the current state. */
+swe_status swe_set_sediment(swe_handle *h, int on);
+
+/* ---------------------------------------------------------------------
+ * Learned bed surrogate (a project addition, not in the paper): a 6-layer
+ * 3x3 convolutional network, 32 channels, BF16 weights and activations with
+ * FP32 accumulation on the tensor cores (tcgen05), that predicts the bed
+ * change over a window of K coupled steps from the state at the window's
+ * start.  Inputs are the solver state cut into T x T tiles (batch index
+ * ty * ceil(nx/T) + tx), channels (H, Hu, Hv, b) normalised with
+ * norm[0..3] (means) and norm[4..7] (standard deviations); the output is the
+ * bed change normalised with norm[8] (mean) and norm[9] (std).  Device
+ * tensors: X bf16 [B][T][T][8] (channels 4..7 zero), targets/outputs
+ * float [B][T][T].  Training: MSE loss, Adam (lr given, betas 0.9/0.999). */
+typedef struct swe_surrogate swe_surrogate;
+typedef struct {
+    int64_t windows, surrogate_windows, plain_windows, judged, takeover_window;
+    double bed_time;          /* simulated seconds the bed advanced */
+    double water_time;        /* simulated seconds the water advanced */
+    double err_last, err_max, err_mean;  /* judged relative L1 error of the bed change */
+    double err_zero_mean;     /* the same for predicting no change (1 by definition) */
+    double err_persist_mean;  /* the same for repeating the last judged change */
+    double elev_err_max;      /* judged relative L1 error of the bed elevation itself */
+    int mode;                 /* 0: surrogate windows, 1: plain (after a takeover) */
+} swe_surrogate_stats;
+
+swe_status swe_surrogate_create(int tile, int max_batch, uint64_t seed, void *cuda_stream, swe_surrogate **out);
+swe_status swe_surrogate_destroy(swe_surrogate *s);
+swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[10]);
+/* Forward pass of B tiles (X device bf16, out device float). */
+swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B);
+/* One training step on B tiles (forward, MSE loss, backward, Adam);
+ * *loss_out (host) gets the mean squared error before the update. */
+swe_status swe_surrogate_train_step(swe_surrogate *s, const void *X, const float *target, int B, float lr,
+                                    float *loss_out);
+/* Layer (0..5) parameters, FP32 host array W[nout][9*cin] then bias[nout]
+ * (cin 8 for layer 0, else 32; nout 1 for layer 5, else 32); dir 0 get, 1 set. */
+swe_status swe_surrogate_params(swe_surrogate *s, int layer, float *host, int dir);
+/* Gradients of the last training step, same layout as swe_surrogate_params. */
+swe_status swe_surrogate_grads(swe_surrogate *s, int layer, float *host);
+/* Device pointer of an internal buffer: 0..4 layer outputs (bf16 NHWC32), 5 the network output. */
+swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **ptr);
+/* The FP32 handle's current state as normalised input tiles (device X);
+ * *batch gets the tile count.  save_bed / pack_target: remember the current
+ * bed, later write the normalised bed change since then (device float). */
+swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, int *batch);
+swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h);
+swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target);
+/* Adds the predicted window bed change to the handle's bed in place. */
+swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h);
+/* Runs nwindows windows of K coupled steps' worth of bed evolution with the
+ * water advanced K/f steps per surrogate window; every judge_every-th window
+ * is run by the plain solver and judged; an error above `bound` hands the
+ * rest to the plain solver.  *st accumulates (zero it before the first call). */
+swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwindows, int K, int f, int judge_every,
+                             double bound, swe_surrogate_stats *st);
+
 /* One-line description of the last error on the handle ("" if none). */
 const char *swe_last_error(const swe_handle *h);
 

@@ -27,6 +27,7 @@ UNITS = {
     "swe_capi.cu": [],
     "swe_noalloc.cu": [],
     "swe_ensemble.cu": ["--use_fast_math"],
+    "nn_kernels.cu": [],
 }
 
 

@@ -523,6 +523,18 @@ extern "C" swe_status swe_set_time(swe_handle *h, double t) {
     return read_dev(h);
 }
 
+extern "C" swe_status swe_set_sediment(swe_handle *h, int on) {
+    if (!h) return SWE_EINVAL;
+    h->c.sediment_on = on ? 1 : 0;
+    h->p.sediment_on = h->c.sediment_on;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    if (!h->state_set) return SWE_OK;
+    // the Eq. 7 maxima depend on the coupling: gather them again for the current state
+    CU(h, L_init(h));
+    CU(h, L_between(h, 2));
+    return read_dev(h);
+}
+
 extern "C" swe_status swe_get_diag(swe_handle *h, swe_diag *out) {
     if (!h || !out) return fail(h, SWE_EINVAL, "swe_get_diag: bad argument");
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_get_diag before swe_set_state");
@@ -586,6 +598,17 @@ bool handle_view(swe_handle *h, SweConst **c, SweBufs **b, cudaStream_t *s, int 
 }
 
 int handle_free_stepping(swe_handle *h) { return (int)free_stepping(h); }
+
+void *handle_current_state(swe_handle *h) {
+    if (!h || !h->state_set || read_dev(h) != SWE_OK) return nullptr;
+    return h->b.buf[h->h_dev->n & 1];
+}
+
+int handle_state_changed(swe_handle *h) {
+    if (!h) return SWE_EINVAL;
+    const size_t nt = (size_t)h->c.tiles_x * h->c.tiles_y;
+    return cudaMemsetAsync(h->b.skipped, 0, nt, h->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
 
 int handle_retile(swe_handle *h, int bw, int th) {
     if (!h || (bw != 128 && bw != 256) || th < 8 || (th % 8) != 0) return SWE_EINVAL;

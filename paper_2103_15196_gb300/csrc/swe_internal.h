@@ -88,6 +88,11 @@ bool handle_view(swe_handle *h, SweConst **c, SweBufs **b, cudaStream_t *s, int 
 int handle_retile(swe_handle *h, int bw, int th);
 // Re-prepares dt without an advance clip (after swe_advance) if needed.
 int handle_free_stepping(swe_handle *h);
+// Device pointer of the current state buffer (synchronises the stream).
+void *handle_current_state(swe_handle *h);
+// The current state was modified outside the step kernels: forget which
+// dry blocks the ping-pong buffers agree on.
+int handle_state_changed(swe_handle *h);
 }  // namespace swe_impl
 
 #define SWE_STATUS_TIMEOUT 4u   // device status bit: a bounded grid barrier gave up

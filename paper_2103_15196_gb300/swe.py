@@ -57,6 +57,20 @@ class Diag(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SurrogateStats(ctypes.Structure):
+    _fields_ = [
+        ("windows", ctypes.c_int64), ("surrogate_windows", ctypes.c_int64), ("plain_windows", ctypes.c_int64),
+        ("judged", ctypes.c_int64), ("takeover_window", ctypes.c_int64),
+        ("bed_time", ctypes.c_double), ("water_time", ctypes.c_double),
+        ("err_last", ctypes.c_double), ("err_max", ctypes.c_double), ("err_mean", ctypes.c_double),
+        ("err_zero_mean", ctypes.c_double), ("err_persist_mean", ctypes.c_double),
+        ("elev_err_max", ctypes.c_double), ("mode", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -107,6 +121,24 @@ def load_library(build_if_missing: bool = True):
         "swe_ensemble_run": [vp, ctypes.c_int64],
         "swe_ensemble_autotune": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "swe_ensemble_set_timeout": [vp, ctypes.c_double, ctypes.c_int],
+    })
+    sig.update({
+        "swe_set_sediment": [H, ctypes.c_int],
+        "swe_surrogate_create": [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(vp)],
+        "swe_surrogate_destroy": [vp],
+        "swe_surrogate_set_norm": [vp, ctypes.POINTER(ctypes.c_float)],
+        "swe_surrogate_forward": [vp, vp, vp, ctypes.c_int],
+        "swe_surrogate_train_step": [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)],
+        "swe_surrogate_params": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int],
+        "swe_surrogate_grads": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
+        "swe_surrogate_buffer": [vp, ctypes.c_int, ctypes.POINTER(vp)],
+        "swe_surrogate_pack_state": [vp, H, vp, ctypes.POINTER(ctypes.c_int)],
+        "swe_surrogate_save_bed": [vp, H],
+        "swe_surrogate_pack_target": [vp, H, vp],
+        "swe_surrogate_apply": [vp, H],
+        "swe_surrogate_run": [vp, H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              ctypes.POINTER(SurrogateStats)],
+        "swe_nn_tc_selftest": [ctypes.c_int, ctypes.c_int, vp, vp, vp],
     })
     for name, args in sig.items():
         f = getattr(L, name)
@@ -261,6 +293,9 @@ class Solver:
         self._check(self._L.swe_get_time(self._h, ctypes.byref(v)))
         return v.value
 
+    def set_sediment(self, on):
+        self._check(self._L.swe_set_sediment(self._h, int(bool(on))))
+
     def set_time(self, t):
         self._check(self._L.swe_set_time(self._h, float(t)))
 
@@ -337,6 +372,101 @@ class Ensemble:
             for m in self.members:
                 m._h = None
             self._L.swe_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """The learned bed surrogate (swe_surrogate_* in include/swe.h).  Tensors
+    passed in are torch CUDA tensors; nothing is computed in Python."""
+
+    CIN = (8, 32, 32, 32, 32, 32)
+    NOUT = (32, 32, 32, 32, 32, 1)
+
+    def __init__(self, tile=1024, max_batch=4, seed=0, stream=None):
+        L = load_library()
+        self._L = L
+        self.tile, self.max_batch = tile, max_batch
+        h = ctypes.c_void_p()
+        st = L.swe_surrogate_create(tile, max_batch, seed, ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if st != SWE_OK:
+            raise SweError(st, "swe_surrogate_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != SWE_OK:
+            raise SweError(st, "surrogate call failed")
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def set_norm(self, norm):
+        a = (ctypes.c_float * 10)(*[float(x) for x in norm])
+        self._check(self._L.swe_surrogate_set_norm(self._h, a))
+
+    def forward(self, X, out, B):
+        self._check(self._L.swe_surrogate_forward(self._h, self._p(X), self._p(out), int(B)))
+
+    def train_step(self, X, target, B, lr):
+        loss = ctypes.c_float(0.0)
+        self._check(self._L.swe_surrogate_train_step(self._h, self._p(X), self._p(target), int(B), float(lr),
+                                                     ctypes.byref(loss)))
+        return loss.value
+
+    def _size(self, layer):
+        return self.NOUT[layer] * 9 * self.CIN[layer] + self.NOUT[layer]
+
+    def params(self, layer):
+        a = np.zeros(self._size(layer), dtype=np.float32)
+        self._check(self._L.swe_surrogate_params(self._h, layer, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0))
+        n = self.NOUT[layer]
+        return a[:-n].reshape(n, -1).copy(), a[-n:].copy()
+
+    def set_params(self, layer, Wm, b):
+        a = np.concatenate([np.asarray(Wm, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+        assert a.size == self._size(layer)
+        self._check(self._L.swe_surrogate_params(self._h, layer, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    def grads(self, layer):
+        a = np.zeros(self._size(layer), dtype=np.float32)
+        self._check(self._L.swe_surrogate_grads(self._h, layer, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        n = self.NOUT[layer]
+        return a[:-n].reshape(n, -1).copy(), a[-n:].copy()
+
+    def buffer_ptr(self, index):
+        p = ctypes.c_void_p()
+        self._check(self._L.swe_surrogate_buffer(self._h, index, ctypes.byref(p)))
+        return p.value
+
+    def pack_state(self, solver, X):
+        b = ctypes.c_int(0)
+        self._check(self._L.swe_surrogate_pack_state(self._h, solver._h, self._p(X), ctypes.byref(b)))
+        return b.value
+
+    def save_bed(self, solver):
+        self._check(self._L.swe_surrogate_save_bed(self._h, solver._h))
+
+    def pack_target(self, solver, target):
+        self._check(self._L.swe_surrogate_pack_target(self._h, solver._h, self._p(target)))
+
+    def apply(self, solver):
+        self._check(self._L.swe_surrogate_apply(self._h, solver._h))
+
+    def run(self, solver, nwindows, K=50, f=10, judge_every=10, bound=0.02, stats=None):
+        st = stats if stats is not None else SurrogateStats()
+        self._check(self._L.swe_surrogate_run(self._h, solver._h, int(nwindows), int(K), int(f), int(judge_every),
+                                              float(bound), ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.swe_surrogate_destroy(self._h)
             self._h = None
 
     def __del__(self):

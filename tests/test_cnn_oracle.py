@@ -1,0 +1,56 @@
+"""Pins of the CPU reference network (oracle/cnn_oracle.py): the convolution
+against scipy's 2D correlation, and the back-propagated gradients against
+central finite differences of the loss."""
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+
+
+def test_conv3x3_matches_scipy_correlate2d():
+    scipy_signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(7, 9, 3))
+    Wm = rng.normal(size=(2, 27))
+    b = np.array([0.3, -0.2])
+    Y = C.conv3x3(X, Wm, b)
+    for n in range(2):
+        ref = np.full((7, 9), b[n])
+        for c in range(3):
+            k = Wm[n].reshape(9, 3)[:, c].reshape(3, 3)       # k[dy+1][dx+1]
+            ref += scipy_signal.correlate2d(X[:, :, c], k, mode="same", boundary="fill")
+        assert np.allclose(Y[:, :, n], ref, atol=1e-12)
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(1)
+    H = W = 6
+    X = np.zeros((H, W, 8))
+    X[:, :, :4] = rng.normal(size=(H, W, 4))
+    target = rng.normal(size=(H, W))
+    params = C.random_params(2)
+    loss, grads, _ = C.loss_and_grads(X, target, params)
+    eps = 1e-6
+    for layer in range(6):
+        Wm, b = params[layer]
+        for _ in range(6):
+            n = rng.integers(Wm.shape[0])
+            k = rng.integers(Wm.shape[1])
+            if layer == 0 and k % 8 >= 4:
+                continue
+            old = Wm[n, k]
+            Wm[n, k] = old + eps
+            lp = C.loss_and_grads(X, target, params)[0]
+            Wm[n, k] = old - eps
+            lm = C.loss_and_grads(X, target, params)[0]
+            Wm[n, k] = old
+            fd = (lp - lm) / (2 * eps)
+            assert grads[layer][0][n, k] == pytest.approx(fd, rel=1e-5, abs=1e-9), (layer, n, k)
+        n = rng.integers(b.shape[0])
+        old = b[n]
+        b[n] = old + eps
+        lp = C.loss_and_grads(X, target, params)[0]
+        b[n] = old - eps
+        lm = C.loss_and_grads(X, target, params)[0]
+        b[n] = old
+        assert grads[layer][1][n] == pytest.approx((lp - lm) / (2 * eps), rel=1e-5, abs=1e-9), layer
