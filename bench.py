@@ -287,6 +287,125 @@ def run_ensemble(args, torch, swe):
                       "n~U[0.02,0.06], peak~U[50,1000], d50 scale~U[0.5,2], FP32, seed 4"}
 
 
+def run_surrogate(args, torch, swe):
+    """Config 5: the learned bed surrogate.  2000 samples (500 snapshots x 4
+    tiles of 1024^2) of (state, bed change over K = 50 steps) from solver runs
+    on the 2048^2 flood-channel terrain class (fractal DEM + carved channel,
+    half wet with a dam-break step, inflow hydrograph), training on the GPU,
+    then an unseen scenario run with surrogate windows (water advanced K/f
+    steps, bed by the network; every judge_every-th window run by the plain
+    solver and judged) against the plain coupled method."""
+    from paper_2103_15196_gb300 import inputs as I
+    K, T, n, f, J = 50, 1024, 2048, args.sur_f, args.sur_judge
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    def scenario(seed):
+        return I.ensemble_scenario(n, seed=seed, manning=0.035, peak=500.0, d50_scale=1.0)
+
+    def solver(sc):
+        S = swe.Solver(n, n, 5.0, precision="fp32", stream=sp)
+        S.set_manning(sc.manning, block=sc.manning_block)
+        S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
+        S.set_state(*(a.astype(np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)))
+        return S
+
+    t_all = time.perf_counter()
+    sv = solver(scenario(7000))
+    sv.run_steps(args.sur_spin)
+    H, Hu, Hv, b0 = sv.get_state(np.float32)
+    sv.run_steps(K)
+    b1 = sv.get_state(np.float32)[3]
+    db = (b1 - b0).astype(np.float64)
+    wet = H > 1e-4
+    sp_ = np.sqrt((np.where(wet, Hu / np.maximum(H, 1e-4), 0) ** 2 + np.where(wet, Hv / np.maximum(H, 1e-4), 0) ** 2))
+    vs = float(np.sqrt(np.mean(sp_[wet] ** 2))) + 1e-6 if wet.any() else 1.0
+    norm = [float(H.mean()), float(Hu.mean()), float(Hv.mean()), float(b0.mean()),
+            float(H.std()) + 1e-6, float(Hu.std()) + 1e-6, float(Hv.std()) + 1e-6, float(b0.std()) + 1e-6,
+            0.0, float(db.std()) + 1e-9, vs, vs ** 3]
+    sv.close()
+    net = swe.Surrogate(tile=T, max_batch=4, seed=0, stream=sp)
+    net.set_norm(norm)
+    nsnap = args.sur_samples // 4
+    X = torch.empty((nsnap * 4, T, T, 8), dtype=torch.bfloat16, device="cuda")
+    Y = torch.empty((nsnap * 4, T, T), dtype=torch.float32, device="cuda")
+    nscen = max(1, nsnap // args.sur_snaps_per_run)
+    k = 0
+    for r in range(nscen):
+        sv = solver(scenario(7100 + r))
+        sv.run_steps(args.sur_spin)
+        for _ in range(nsnap // nscen if r < nscen - 1 else nsnap - k):
+            net.save_bed(sv)
+            net.pack_state(sv, X[4 * k:4 * k + 4])
+            sv.run_steps(K)
+            net.pack_target(sv, Y[4 * k:4 * k + 4])
+            k += 1
+        sv.close()
+    t_data = time.perf_counter() - t_all
+    # training
+    t0 = time.perf_counter()
+    g = torch.Generator().manual_seed(0)
+    steps, first, last = 0, None, None
+    lr0 = args.sur_lr
+    while time.perf_counter() - t0 < args.sur_train_seconds:
+        for i in torch.randperm(nsnap, generator=g).tolist():
+            frac = min(1.0, (time.perf_counter() - t0) / args.sur_train_seconds)
+            loss = net.train_step(X[4 * i:4 * i + 4], Y[4 * i:4 * i + 4], 4, lr0 * (0.1 + 0.9 * (1 - frac)))
+            first = loss if first is None else first
+            last = loss
+            steps += 1
+            if time.perf_counter() - t0 >= args.sur_train_seconds:
+                break
+    t_train = time.perf_counter() - t0
+    # forward time of one 2048^2 domain (4 tiles)
+    outb = torch.empty((4, T, T), dtype=torch.float32, device="cuda")
+    net.forward(X[0:4], outb, 4)
+    fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fa.record(stream)
+    for _ in range(5):
+        net.forward(X[0:4], outb, 4)
+    fb.record(stream)
+    fb.synchronize()
+    fwd_ms = fa.elapsed_time(fb) / 5
+    del X, Y, outb
+    torch.cuda.empty_cache()
+    # evaluation on an unseen scenario: plain coupled method vs surrogate windows
+    sc = scenario(7999)
+    R = args.sur_windows
+    A = solver(sc)
+    A.run_steps(args.sur_spin)
+    A.sync()
+    ta = A.t
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    A.run_steps(K * R)
+    e1.record(stream)
+    e1.synchronize()
+    wall_p = e0.elapsed_time(e1) * 1e-3
+    bed_p = A.t - ta
+    A.close()
+    Bs = solver(sc)
+    Bs.run_steps(args.sur_spin)
+    Bs.sync()
+    w0 = time.perf_counter()
+    st = net.run(Bs, R, K=K, f=f, judge_every=J, bound=args.sur_bound)
+    wall_s = time.perf_counter() - w0
+    Bs.close()
+    net.close()
+    rate_p = bed_p / wall_p
+    rate_s = st.bed_time / wall_s
+    out = {"metric": "surrogate bed simulated-time rate / plain method's, at judged error",
+           "speedup": rate_s / rate_p, "rate_plain_s_per_s": rate_p, "rate_surrogate_s_per_s": rate_s,
+           "K": K, "f": f, "judge_every": J, "bound": args.sur_bound, "windows": R,
+           "stats": st.as_dict(), "train_steps": steps, "train_loss_first": first, "train_loss_last": last,
+           "samples": nsnap * 4, "tile": T, "forward_ms_2048sq": fwd_ms,
+           "plain_window_ms": wall_p * 1e3 / R,
+           "seconds": {"data": t_data, "train": t_train, "eval": wall_p + wall_s},
+           "error_metric": "err_*: relative L1 of the predicted bed change against the plain solver's over the "
+                           "judged window; elev_err_max: relative L1 of the bed elevation"}
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2103_15196_gb300 import swe
@@ -369,6 +488,9 @@ def run_ours(args):
     ens = None
     if world == 1 and not args.no_ensemble:
         ens = run_ensemble(args, torch, swe)
+    sur = None
+    if world == 1 and not args.no_surrogate:
+        sur = run_surrogate(args, torch, swe)
 
     if rank != 0:
         if world > 1:
@@ -403,6 +525,7 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cb,
         "ensemble": ens,
+        "surrogate": sur,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -428,9 +551,24 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-only", action="store_true", help="run only the config-5 surrogate experiment")
+    ap.add_argument("--sur-samples", type=int, default=2000)
+    ap.add_argument("--sur-snaps-per-run", type=int, default=100)
+    ap.add_argument("--sur-spin", type=int, default=300)
+    ap.add_argument("--sur-train-seconds", type=float, default=60.0)
+    ap.add_argument("--sur-lr", type=float, default=1e-3)
+    ap.add_argument("--sur-windows", type=int, default=40)
+    ap.add_argument("--sur-f", type=int, default=10)
+    ap.add_argument("--sur-judge", type=int, default=10)
+    ap.add_argument("--sur-bound", type=float, default=0.5)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.surrogate_only:
+        import torch
+        from paper_2103_15196_gb300 import swe
+        print(json.dumps({"surrogate": run_surrogate(args, torch, swe)}), flush=True)
     else:
         run_ours(args)
 

@@ -249,10 +249,11 @@ swe_status swe_set_sediment(swe_handle *h, int on);
  * FP32 accumulation on the tensor cores (tcgen05), that predicts the bed
  * change over a window of K coupled steps from the state at the window's
  * start.  Inputs are the solver state cut into T x T tiles (batch index
- * ty * ceil(nx/T) + tx), channels (H, Hu, Hv, b) normalised with
- * norm[0..3] (means) and norm[4..7] (standard deviations); the output is the
- * bed change normalised with norm[8] (mean) and norm[9] (std).  Device
- * tensors: X bf16 [B][T][T][8] (channels 4..7 zero), targets/outputs
+ * ty * ceil(nx/T) + tx) with 8 channels: (H, Hu, Hv, b) normalised with
+ * norm[0..3] (means) and norm[4..7] (standard deviations), the cell velocity
+ * (u, v) / norm[10], and the Shamov-gated Grass direction v|v|^2 (Eq. 3-5)
+ * / norm[11].  The output is the bed change normalised with norm[8] (mean)
+ * and norm[9] (std).  Device tensors: X bf16 [B][T][T][8], targets/outputs
  * float [B][T][T].  Training: MSE loss, Adam (lr given, betas 0.9/0.999). */
 typedef struct swe_surrogate swe_surrogate;
 typedef struct {
@@ -268,7 +269,7 @@ typedef struct {
 
 swe_status swe_surrogate_create(int tile, int max_batch, uint64_t seed, void *cuda_stream, swe_surrogate **out);
 swe_status swe_surrogate_destroy(swe_surrogate *s);
-swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[10]);
+swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[12]);
 /* Forward pass of B tiles (X device bf16, out device float). */
 swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B);
 /* One training step on B tiles (forward, MSE loss, backward, Adam);

@@ -1,6 +1,7 @@
 // Tensor-core kernels of the learned bed surrogate (BF16 operands, FP32
 // accumulation in tensor memory), plus a self-test GEMM of the same MMA path.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "../../include/swe.h"
@@ -52,10 +53,10 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const __nv_bfloat16 *_
         }
         mma_commit(mbar);
     }
-    bool ok = mbar_wait(mbar, 0, kPolls);
+    bool ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));
     if (!ok) {
-        atomicOr(err, 1);
-        ok = mbar_wait(mbar, 0, kPolls);   // let MMAs in flight finish before freeing TMEM
+        if (t == 0) atomicOr(err, 1);
+        ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));   // let MMAs in flight finish before freeing TMEM
     }
     tc_fence_after();
     if (ok) {
@@ -192,10 +193,10 @@ conv3x3_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict_
         }
         mma_commit(mbar);
     }
-    bool ok = mbar_wait(mbar, 0, kPolls);
+    bool ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));
     if (!ok) {
-        atomicOr(err, 1);
-        ok = mbar_wait(mbar, 0, kPolls);
+        if (t == 0) atomicOr(err, 1);
+        ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));
     }
     tc_fence_after();
     if (ok) {
@@ -227,6 +228,331 @@ conv3x3_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict_
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
+// cp.async of 16 bytes into shared memory; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Persistent form of conv3x3_tc: one CTA per SM keeps the weights in shared
+// memory and walks 128-pixel tiles (round-robin over the grid).  Two A
+// buffers and two TMEM accumulator halves pipeline the work: while the MMAs
+// of tile i run, the CTA stores the result of tile i-1 and streams the im2col
+// of tile i+1 in with cp.async.
+template <int CIN, int NOUT, int EPI>
+__global__ void __launch_bounds__(128, 1)
+conv3x3_tcp(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
+            const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf, int H,
+            int W, int nimg, int *err) {
+    constexpr int KP = ConvK<CIN>::KP;
+    constexpr int ABYTES = 128 * KP * 2;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sa0 = sm;
+    unsigned char *sa1 = sm + ABYTES;
+    unsigned char *sb = sm + 2 * ABYTES;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NOUT * KP * 2);   // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int segs = (W + 127) / 128;
+    const long long ntile = (long long)nimg * H * segs;
+    const size_t plane = (size_t)H * W;
+
+    // weights, and the zero K-padding columns of both A buffers
+    for (int i = t; i < NOUT * (KP / 8); i += 128) {
+        const int r = i / (KP / 8), c = i % (KP / 8);
+        *reinterpret_cast<uint4 *>(sb + kmajor_off(r, c * 8, NOUT)) =
+            *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KP + c * 8);
+    }
+    for (int k = 9 * CIN; k < KP; k += 8) {
+        *reinterpret_cast<uint4 *>(sa0 + kmajor_off(t, k, 128)) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4 *>(sa1 + kmajor_off(t, k, 128)) = make_uint4(0, 0, 0, 0);
+    }
+
+    auto load_tile = [&](long long tile, unsigned char *sa) {
+        const int img = (int)(tile / ((long long)H * segs));
+        const int rem = (int)(tile % ((long long)H * segs));
+        const int y = rem / segs, x0 = (rem % segs) * 128;
+        const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
+        if (CIN == 32) {
+            const int cg = t & 3, pb = t >> 2;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int yy = y + tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int p = pb + 32 * pp, xx = x0 + p + dx;
+                    const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                    const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN + cg * 8 : X;
+                    cp_async16(sa + kmajor_off(p, tap * CIN + cg * 8, 128), src, in ? 16 : 0);
+                }
+            }
+        } else {
+            const int p = t;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int yy = y + tap / 3 - 1, xx = x0 + p + tap % 3 - 1;
+                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN : X;
+                cp_async16(sa + kmajor_off(p, tap * CIN, 128), src, in ? 16 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    auto epilogue = [&](long long tile, uint32_t taddr) {
+        const int img = (int)(tile / ((long long)H * segs));
+        const int rem = (int)(tile % ((long long)H * segs));
+        const int y = rem / segs, x0 = (rem % segs) * 128;
+        float v[32];
+        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
+        const int p = warp * 32 + lane, xx = x0 + p;
+        if (xx >= W) return;
+        const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
+        if (EPI == EPI_OUT) {
+            Yf[pix] = v[0] + bias[0];
+        } else {
+            __align__(16) __nv_bfloat16 o[32];
+            if (EPI == EPI_RELU) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(fmaxf(v[j] + bias[j], 0.f));
+            } else {
+                __align__(16) __nv_bfloat16 m[32];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(m)[q] = reinterpret_cast<const uint4 *>(mask + pix * 32)[q];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(__bfloat162float(m[j]) > 0.f ? v[j] : 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(Y + pix * 32)[q] = reinterpret_cast<uint4 *>(o)[q];
+        }
+    };
+
+    if (warp == 0) tmem_alloc(tslot, 64);
+    if (t == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
+    long long tile = blockIdx.x;
+    if (tile < ntile) load_tile(tile, sa0);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t ph[2] = {0, 0};
+    bool ok = true;
+    long long prev = -1;
+    int it = 0;
+    for (; tile < ntile && ok; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        unsigned char *sa = buf ? sa1 : sa0;
+        cp_async_wait_all();
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < KP / 16; ++kk) {
+                const uint64_t ad = smem_desc(smem_u32(sa) + kk * 128 * 32, 128 * 16, 128);
+                const uint64_t bd = smem_desc(smem_u32(sb) + kk * NOUT * 32, NOUT * 16, 128);
+                mma_bf16(tmem + buf * 32, ad, bd, idesc_bf16_f32(NOUT), kk > 0 ? 1u : 0u);
+            }
+            mma_commit(&mbar[buf]);
+        }
+        if (prev >= 0) {
+            const int pb = buf ^ 1;
+            ok = __syncthreads_and(mbar_wait(&mbar[pb], ph[pb], kPolls));
+            ph[pb] ^= 1;
+            tc_fence_after();
+            if (ok) epilogue(prev, tmem + pb * 32);
+        }
+        const long long next = tile + gridDim.x;
+        if (ok && next < ntile) load_tile(next, buf ? sa0 : sa1);
+        prev = tile;
+    }
+    if (ok && prev >= 0) {
+        const int pb = (it - 1) & 1;
+        ok = __syncthreads_and(mbar_wait(&mbar[pb], ph[pb], kPolls));
+        ph[pb] ^= 1;
+        tc_fence_after();
+        if (ok) epilogue(prev, tmem + pb * 32);
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(err, 1);
+        __syncthreads_and(mbar_wait(&mbar[0], ph[0], kPolls));
+        __syncthreads_and(mbar_wait(&mbar[1], ph[1], kPolls));
+    }
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+// Row-streaming form of the convolution (used by the surrogate): no im2col.
+// A CTA owns one 128-pixel column band of an image and a run of output rows.
+// Each input row it needs is loaded once, into a shared-memory slot of 136
+// pixels (x0-1 .. x0+134) in the K-major layout, the 136 rows of each 8-channel
+// column block contiguous (16 bytes per pixel, blocks CBS bytes apart).  The
+// A operand of tap (dy, dx) is then that slot read from pixel dx+1 on: the
+// same layout with the descriptor's start moved by 16 (dx+1) bytes.  With 32
+// channels a tap is two MMAs (K = 16 channels each, LBO = CBS); with 8
+// channels one MMA covers the taps (dy, dx) and (dy, dx+1), LBO = 16 bytes
+// (one pixel), and the weights carry a zero block for the unused pair
+// partner.  Five row slots and two TMEM accumulator halves pipeline the rows:
+// while the MMAs of row y run, the CTA stores row y-1, and rows y+2 and y+3
+// stream in with cp.async.
+template <int CIN> struct RowConv {
+    static constexpr int KR = CIN == 8 ? 96 : 9 * CIN;   // K of the MMA sequence
+    static constexpr int RP = 136;                        // pixels per row slot
+    static constexpr int CBS = RP * 16 + 16;              // column-block stride (padded against bank conflicts)
+    static constexpr int SLOT = (CIN / 8) * CBS;
+    static constexpr int NS = 5;                          // row slots
+    template <int NOUT> static constexpr size_t smem() { return (size_t)NOUT * KR * 2 + (size_t)NS * SLOT + 64; }
+};
+
+template <int CIN, int NOUT, int EPI>
+__global__ void __launch_bounds__(128)
+conv3x3_row(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
+            const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf, int H,
+            int W, int rows, int *err) {
+    using RC = RowConv<CIN>;
+    constexpr int KPS = ConvK<CIN>::KP;
+    constexpr int KR = RC::KR, NMMA = KR / 16, CB = CIN / 8, CBS = RC::CBS, SLOT = RC::SLOT, NS = RC::NS;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sb = sm;                       // NOUT x KR
+    unsigned char *slots = sm + NOUT * KR * 2;    // NS x SLOT
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(slots + NS * SLOT);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int x0 = blockIdx.x * 128, ya = blockIdx.y * rows, img = blockIdx.z;
+    const int yb = min(ya + rows, H);
+    const size_t plane = (size_t)H * W;
+    const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
+
+    // weights, in the order of the MMA sequence
+    for (int i = t; i < NOUT * (KR / 8); i += 128) {
+        const int r = i / (KR / 8), kb = i % (KR / 8);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (CIN == 8) {
+            const int dyi = kb / 4, dxs = kb % 4;
+            if (dxs < 3) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KPS + (dyi * 3 + dxs) * 8);
+        } else {
+            v = *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KPS + kb * 8);
+        }
+        *reinterpret_cast<uint4 *>(sb + kmajor_off(r, kb * 8, NOUT)) = v;
+    }
+
+    // slot of input row yy (yy >= -1)
+    auto slot_of = [&](int yy) { return slots + ((yy + NS) % NS) * SLOT; };
+    // one cp.async group per call (empty when the row is not needed)
+    auto load_row = [&](int yy, bool need) {
+        if (need) {
+            unsigned char *slot = slot_of(yy);
+            const bool rin = yy >= 0 && yy < H;
+            for (int i = t; i < RC::RP * CB; i += 128) {
+                const int j = i / CB, cb = i % CB;
+                const int xx = x0 - 1 + j;
+                const bool in = rin && xx >= 0 && xx < W;
+                const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN + cb * 8 : X;
+                cp_async16(slot + cb * CBS + j * 16, src, in ? 16 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    auto epilogue = [&](int y, uint32_t taddr) {
+        float v[32];
+        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
+        const int p = warp * 32 + lane, xx = x0 + p;
+        if (xx >= W) return;
+        const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
+        if (EPI == EPI_OUT) {
+            Yf[pix] = v[0] + bias[0];
+        } else {
+            __align__(16) __nv_bfloat16 o[32];
+            if (EPI == EPI_RELU) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(fmaxf(v[jj] + bias[jj], 0.f));
+            } else {
+                __align__(16) __nv_bfloat16 m[32];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(m)[q] = reinterpret_cast<const uint4 *>(mask + pix * 32)[q];
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(__bfloat162float(m[jj]) > 0.f ? v[jj] : 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(Y + pix * 32)[q] = reinterpret_cast<uint4 *>(o)[q];
+        }
+    };
+
+    if (warp == 0) tmem_alloc(tslot, 64);
+    if (t == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
+    load_row(ya - 1, true);
+    load_row(ya, true);
+    load_row(ya + 1, true);
+    load_row(ya + 2, ya + 2 <= yb);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phases = 0;   // bit h: parity of the next phase of mbar[h]
+    bool ok = true;
+    int it = 0;
+    for (int y = ya; y < yb && ok; ++y, ++it) {
+        const int half = it & 1;
+        // rows y-1 .. y+1 have landed (only the group of row y+2 may be pending)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
+#pragma unroll 1
+            for (int m = 0; m < NMMA; ++m) {
+                uint32_t astart, lbo;
+                if (CIN == 8) {
+                    const int dyi = m / 2, pair = m % 2;
+                    astart = smem_u32(slot_of(y + dyi - 1)) + pair * 2 * 16;
+                    lbo = 16;
+                } else {
+                    const int tap = m / 2, hc = m % 2, dyi = tap / 3, dxi = tap % 3;
+                    astart = smem_u32(slot_of(y + dyi - 1)) + hc * 2 * CBS + dxi * 16;
+                    lbo = CBS;
+                }
+                const uint64_t ad = smem_desc(astart, lbo, 128);
+                const uint64_t bd = smem_desc(smem_u32(sb) + m * NOUT * 32, NOUT * 16, 128);
+                mma_bf16(tmem + half * 32, ad, bd, idesc_bf16_f32(NOUT), m > 0 ? 1u : 0u);
+            }
+            mma_commit(&mbar[half]);
+        }
+        if (it > 0) {
+            const int pb = half ^ 1;
+            ok = __syncthreads_and(mbar_wait(&mbar[pb], (phases >> pb) & 1u, kPolls));
+            phases ^= 1u << pb;
+            tc_fence_after();
+            if (ok) epilogue(y - 1, tmem + pb * 32);
+        }
+        // the slot of row y+3 held row y-2, last read by the MMAs of row y-1
+        if (ok) load_row(y + 3, y + 3 <= yb);
+    }
+    if (ok && it > 0) {
+        const int pb = (it - 1) & 1;
+        ok = __syncthreads_and(mbar_wait(&mbar[pb], (phases >> pb) & 1u, kPolls));
+        phases ^= 1u << pb;
+        tc_fence_after();
+        if (ok) epilogue(yb - 1, tmem + pb * 32);
+    }
+    if (!ok) {
+        // let MMAs in flight finish before the tensor memory is freed
+        if (t == 0) atomicOr(err, 1);
+        __syncthreads_and(mbar_wait(&mbar[0], phases & 1u, kPolls));
+        __syncthreads_and(mbar_wait(&mbar[1], (phases >> 1) & 1u, kPolls));
+    }
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
 // Weight gradient: dW[k][n] = sum_p Xpatch[p][k] dY[p][n] (k = tap*CIN + c;
@@ -331,14 +657,14 @@ wgrad_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ 
                 mma_commit(mbar);
             }
             first = false;
-            ok = mbar_wait(mbar, phase, kPolls);
+            ok = __syncthreads_and(mbar_wait(mbar, phase, kPolls));
             phase ^= 1;
             tc_fence_after();
         }
     }
     if (!ok) {
-        atomicOr(err, 1);
-        mbar_wait(mbar, phase ^ 1, kPolls);
+        if (t == 0) atomicOr(err, 1);
+        __syncthreads_and(mbar_wait(mbar, phase ^ 1, kPolls));
     }
     if (ok && !first) {
         float *out = partial + ((size_t)img * gridDim.x + blockIdx.x) * (MT * 128) * NOUT;
@@ -447,10 +773,13 @@ __global__ void loss_grad(const float *__restrict__ out, const float *__restrict
 }
 
 // Solver state (AoS float4 {H, Hu, Hv, b}, nx x ny) -> NHWC8 BF16 tiles of
-// T x T (tile (tx, ty) of the domain -> batch index ty * ntx + tx), channels
-// (H, Hu, Hv, b) normalised as (x - mean) / std, zeros beyond the domain.
+// T x T (tile (tx, ty) of the domain -> batch index ty * ntx + tx), zeros
+// beyond the domain.  Channels: (H, Hu, Hv, b) normalised as
+// (x - norm[j]) / norm[4 + j]; the cell velocity (u, v) / norm[10]; and the
+// Grass load direction of Eq. 3 with m = 2, v |v|^2, where the Shamov gate of
+// Eq. 5 is open (|v|^6 > ksh H), over norm[11].  Dry cells: zero velocity.
 __global__ void pack_state(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ norm,
-                           __nv_bfloat16 *__restrict__ X, size_t total) {
+                           float eps, float ksh, __nv_bfloat16 *__restrict__ X, size_t total) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t plane = (size_t)T * T;
         const int bt = (int)(i / plane);
@@ -463,8 +792,17 @@ __global__ void pack_state(const float4 *__restrict__ state, int nx, int ny, int
         const float f[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = __float2bfloat16(in ? (f[j] - norm[j]) / norm[4 + j] : 0.f);
-#pragma unroll
-        for (int j = 4; j < 8; ++j) o[j] = __float2bfloat16(0.f);
+        float u = 0.f, v = 0.f, jx = 0.f, jy = 0.f;
+        if (in && c.x > eps) {
+            u = c.y / c.x;
+            v = c.z / c.x;
+            const float s2 = u * u + v * v;
+            if (s2 * s2 * s2 > ksh * c.x) { jx = u * s2; jy = v * s2; }
+        }
+        o[4] = __float2bfloat16(u / norm[10]);
+        o[5] = __float2bfloat16(v / norm[10]);
+        o[6] = __float2bfloat16(jx / norm[11]);
+        o[7] = __float2bfloat16(jy / norm[11]);
         reinterpret_cast<uint4 *>(X)[i] = reinterpret_cast<uint4 *>(o)[0];
     }
 }
@@ -491,6 +829,7 @@ __global__ void apply_bed(float4 *__restrict__ state, int nx, int ny, int T, int
 // ======================================================================
 
 #include <cmath>
+#include <cstdlib>
 #include <random>
 #include <vector>
 
@@ -524,7 +863,7 @@ struct swe_surrogate {
     size_t partial_floats = 0;
     long adam_t = 0;
     std::vector<void *> allocs;
-    float h_norm[10] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 1};
+    float h_norm[12] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 1, 1, 1};
 };
 
 namespace {
@@ -537,9 +876,37 @@ cudaError_t salloc(swe_surrogate *s, void **p, size_t bytes) {
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
+int g_persist = -1;   // 1: persistent pipelined convolutions (default), 0: one CTA per tile
+
 template <int CIN, int NOUT, int EPI>
 cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, const __nv_bfloat16 *Wt, const float *bias,
                  const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B) {
+    if (g_persist < 0) {
+        // SWE_NN_CONV: 1 row-streaming (default), 2 persistent im2col, 0 one CTA per tile
+        const char *e = getenv("SWE_NN_CONV");
+        g_persist = (e && (e[0] == '0' || e[0] == '2')) ? e[0] - '0' : 1;
+    }
+    if (g_persist == 1) {
+        // row-streaming kernel
+        // at least 30 KB: at most 7 CTAs (448 TMEM columns) per SM
+        const size_t smem = std::max<size_t>(RowConv<CIN>::template smem<NOUT>(), 30 * 1024);
+        cudaFuncSetAttribute(conv3x3_row<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int rows = 16;
+        dim3 grid((s->T + 127) / 128, (s->T + rows - 1) / rows, B);
+        conv3x3_row<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
+        return cudaGetLastError();
+    }
+    if (g_persist == 2) {
+        const size_t smem = (size_t)(2 * 128 + NOUT) * ConvK<CIN>::KP * 2 + 64;
+        cudaFuncSetAttribute(conv3x3_tcp<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long ntile = (long long)B * s->T * ((s->T + 127) / 128);
+        const int grid = (int)std::min<long long>(ntile, sms);
+        conv3x3_tcp<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, B, s->err);
+        return cudaGetLastError();
+    }
     const size_t smem = conv_smem<CIN, NOUT, EPI>();
     cudaFuncSetAttribute(conv3x3_tc<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((s->T + 127) / 128, s->T, B);
@@ -630,12 +997,13 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
         if (e == cudaSuccess) e = salloc(s, (void **)&l.grad, (size_t)l.mt * 128 * l.noutp * 4);
         // He initialisation for the hidden layers, a small output layer
         std::vector<float> w(nw);
-        const int fan_in = 9 * (i == 0 ? 4 : l.cin);
+        const int fan_in = 9 * l.cin;
         const float sd = i == 5 ? 0.01f : std::sqrt(2.f / fan_in);
         for (int n = 0; n < l.nout; ++n)
             for (int k = 0; k < 9 * l.cin; ++k) {
                 const int c = k % l.cin;
-                w[(size_t)n * 9 * l.cin + k] = (i == 0 && c >= 4) ? 0.f : sd * nd(rng);
+                (void)c;
+                w[(size_t)n * 9 * l.cin + k] = sd * nd(rng);
             }
         if (e == cudaSuccess) e = cudaMemcpyAsync(l.Wm, w.data(), nw * 4, cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess) e = prep(s, l);
@@ -655,7 +1023,7 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
     if (e == cudaSuccess) e = salloc(s, (void **)&s->loss, 16);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->norm, 64);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->err, 16);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->norm, s->h_norm, 40, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->norm, s->h_norm, 48, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         swe_surrogate_destroy(s);
@@ -665,13 +1033,12 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
     return SWE_OK;
 }
 
-extern "C" swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[10]) {
+extern "C" swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[12]) {
     if (!s || !norm) return SWE_EINVAL;
-    for (int j = 4; j < 8; ++j)
+    for (int j : {4, 5, 6, 7, 9, 10, 11})
         if (!(norm[j] > 0)) return SWE_EINVAL;
-    if (!(norm[9] > 0)) return SWE_EINVAL;
-    std::copy(norm, norm + 10, s->h_norm);
-    if (cudaMemcpyAsync(s->norm, s->h_norm, 40, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return SWE_ECUDA;
+    std::copy(norm, norm + 12, s->h_norm);
+    if (cudaMemcpyAsync(s->norm, s->h_norm, 48, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return SWE_ECUDA;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
@@ -783,7 +1150,7 @@ extern "C" swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, 
     if (ntx * nty > s->maxB) return SWE_EINVAL;
     const size_t total = (size_t)ntx * nty * s->T * s->T;
     pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm,
-                                                     (__nv_bfloat16 *)X, total);
+                                                     c->eps_f, c->f.ksh, (__nv_bfloat16 *)X, total);
     if (batch) *batch = ntx * nty;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
@@ -842,7 +1209,8 @@ extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
     if (ntx * nty > s->maxB) return SWE_EINVAL;
     const int B = ntx * nty;
     const size_t total = (size_t)B * s->T * s->T;
-    pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, s->X0, total);
+    pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
+                                                     c->f.ksh, s->X0, total);
     if (forward_all(s, s->X0, s->out, B) != cudaSuccess) return SWE_ECUDA;
     apply_bed<<<grid_n(total), 256, 0, s->stream>>>((float4 *)cur, c->nx, c->ny, s->T, ntx, s->out, s->norm, total);
     if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
@@ -927,7 +1295,8 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             ++st->plain_windows;
         } else if (w % judge_every == 0) {                       // judged window
             handle_state(h, &c, &cur, &hs);
-            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, s->X0, total);
+            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
+                                                     c->f.ksh, s->X0, total);
             bed_tiles<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->bsave, total);
             if (forward_all(s, s->X0, s->out, B) != cudaSuccess) { rc = SWE_ECUDA; break; }
             if ((rc = check_err(s)) != SWE_OK) break;
@@ -958,7 +1327,8 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             if (err > bound) { st->mode = 1; st->takeover_window = w; }
         } else {                                                 // surrogate window
             handle_state(h, &c, &cur, &hs);
-            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, s->X0, total);
+            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
+                                                     c->f.ksh, s->X0, total);
             if (forward_all(s, s->X0, s->out, B) != cudaSuccess) { rc = SWE_ECUDA; break; }
             if ((rc = check_err(s)) != SWE_OK) break;
             if ((rc = swe_set_sediment(h, 0)) != SWE_OK) break;

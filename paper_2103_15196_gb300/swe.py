@@ -407,7 +407,7 @@ class Surrogate:
         return ctypes.c_void_p(t.data_ptr())
 
     def set_norm(self, norm):
-        a = (ctypes.c_float * 10)(*[float(x) for x in norm])
+        a = (ctypes.c_float * 12)(*[float(x) for x in norm])
         self._check(self._L.swe_surrogate_set_norm(self._h, a))
 
     def forward(self, X, out, B):
