@@ -320,9 +320,8 @@ def run_surrogate(args, torch, swe):
     wet = H > 1e-4
     sp_ = np.sqrt((np.where(wet, Hu / np.maximum(H, 1e-4), 0) ** 2 + np.where(wet, Hv / np.maximum(H, 1e-4), 0) ** 2))
     vs = float(np.sqrt(np.mean(sp_[wet] ** 2))) + 1e-6 if wet.any() else 1.0
-    norm = [float(H.mean()), float(Hu.mean()), float(Hv.mean()), float(b0.mean()),
-            float(H.std()) + 1e-6, float(Hu.std()) + 1e-6, float(Hv.std()) + 1e-6, float(b0.std()) + 1e-6,
-            0.0, float(db.std()) + 1e-9, vs, vs ** 3]
+    norm = [float(H.mean()), float(H.std()) + 1e-6, float(b0.mean()), float(b0.std()) + 1e-6,
+            vs, vs ** 3, float(db.std()) + 1e-9, (float(db.std()) + 1e-9) / K]
     sv.close()
     net = swe.Surrogate(tile=T, max_batch=4, seed=0, stream=sp)
     net.set_norm(norm)
@@ -335,9 +334,12 @@ def run_surrogate(args, torch, swe):
         sv = solver(scenario(7100 + r))
         sv.run_steps(args.sur_spin)
         for _ in range(nsnap // nscen if r < nscen - 1 else nsnap - k):
+            # a window: its start bed, one coupled step (the network's input
+            # state), then the rest of the K coupled steps (the target)
             net.save_bed(sv)
+            sv.run_steps(1)
             net.pack_state(sv, X[4 * k:4 * k + 4])
-            sv.run_steps(K)
+            sv.run_steps(K - 1)
             net.pack_target(sv, Y[4 * k:4 * k + 4])
             k += 1
         sv.close()

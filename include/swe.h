@@ -247,14 +247,23 @@ swe_status swe_set_sediment(swe_handle *h, int on);
  * Learned bed surrogate (a project addition, not in the paper): a 6-layer
  * 3x3 convolutional network, 32 channels, BF16 weights and activations with
  * FP32 accumulation on the tensor cores (tcgen05), that predicts the bed
- * change over a window of K coupled steps from the state at the window's
- * start.  Inputs are the solver state cut into T x T tiles (batch index
- * ty * ceil(nx/T) + tx) with 8 channels: (H, Hu, Hv, b) normalised with
- * norm[0..3] (means) and norm[4..7] (standard deviations), the cell velocity
- * (u, v) / norm[10], and the Shamov-gated Grass direction v|v|^2 (Eq. 3-5)
- * / norm[11].  The output is the bed change normalised with norm[8] (mean)
- * and norm[9] (std).  Device tensors: X bf16 [B][T][T][8], targets/outputs
- * float [B][T][T].  Training: MSE loss, Adam (lr given, betas 0.9/0.999). */
+ * change over a window of K coupled steps (Eq. 1-6) from the state one
+ * coupled step into the window.  Inputs are the solver state cut into T x T
+ * tiles (batch index ty * ceil(nx/T) + tx) with 8 channels:
+ *   0  (H - norm[0]) / norm[1]         1  (b - norm[2]) / norm[3]
+ *   2  u / norm[4]                     3  v / norm[4]
+ *   4, 5  the Shamov-gated Grass direction v|v|^2 (Eq. 3-5) / norm[5]
+ *   6  p = (b - b_saved) / norm[7]: the first step's bed change, scaled so
+ *      that p is the linear extrapolation of the window's change in output
+ *      units (norm[7] = norm[6] / K)
+ *   7  m = 1 where a cell within 4 cells (Chebyshev distance) changed its
+ *      bed in the first step, else 0 (the activity mask)
+ * b_saved is the bed at the last swe_surrogate_save_bed call (the window's
+ * start).  The network output is m (c + p), c the last convolution: a
+ * learned correction of the linear extrapolation, zero where nothing moved.
+ * Output unit: norm[6] metres of bed change.  Device tensors: X bf16
+ * [B][T][T][8], targets/outputs float [B][T][T].  Training: MSE loss, Adam
+ * (lr given, betas 0.9/0.999). */
 typedef struct swe_surrogate swe_surrogate;
 typedef struct {
     int64_t windows, surrogate_windows, plain_windows, judged, takeover_window;
@@ -263,13 +272,15 @@ typedef struct {
     double err_last, err_max, err_mean;  /* judged relative L1 error of the bed change */
     double err_zero_mean;     /* the same for predicting no change (1 by definition) */
     double err_persist_mean;  /* the same for repeating the last judged change */
+    double err_linear_mean;   /* the same for the linear extrapolation p alone */
     double elev_err_max;      /* judged relative L1 error of the bed elevation itself */
     int mode;                 /* 0: surrogate windows, 1: plain (after a takeover) */
 } swe_surrogate_stats;
 
 swe_status swe_surrogate_create(int tile, int max_batch, uint64_t seed, void *cuda_stream, swe_surrogate **out);
 swe_status swe_surrogate_destroy(swe_surrogate *s);
-swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[12]);
+/* The 8 normalisation constants above; norm[1], norm[3..7] must be > 0. */
+swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[8]);
 /* Forward pass of B tiles (X device bf16, out device float). */
 swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B);
 /* One training step on B tiles (forward, MSE loss, backward, Adam);
@@ -283,18 +294,25 @@ swe_status swe_surrogate_params(swe_surrogate *s, int layer, float *host, int di
 swe_status swe_surrogate_grads(swe_surrogate *s, int layer, float *host);
 /* Device pointer of an internal buffer: 0..4 layer outputs (bf16 NHWC32), 5 the network output. */
 swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **ptr);
-/* The FP32 handle's current state as normalised input tiles (device X);
- * *batch gets the tile count.  save_bed / pack_target: remember the current
- * bed, later write the normalised bed change since then (device float). */
+/* save_bed remembers the FP32 handle's current bed (the window's start);
+ * pack_state writes the handle's current state as input tiles (device X,
+ * channels as above, relative to the saved bed); *batch gets the tile count;
+ * pack_target writes the bed change since save_bed in output units (device
+ * float). */
 swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, int *batch);
 swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h);
 swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target);
-/* Adds the predicted window bed change to the handle's bed in place. */
+/* Predicts the window's bed change from the handle's current state and sets
+ * the bed to the saved bed plus that change. */
 swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h);
-/* Runs nwindows windows of K coupled steps' worth of bed evolution with the
- * water advanced K/f steps per surrogate window; every judge_every-th window
- * is run by the plain solver and judged; an error above `bound` hands the
- * rest to the plain solver.  *st accumulates (zero it before the first call). */
+/* Runs nwindows windows, each worth K coupled steps of bed evolution.  A
+ * surrogate window saves the bed, runs one coupled step, predicts the
+ * window's bed change, advances the water K/f - 1 further steps with the
+ * Exner coupling off and sets the bed to the prediction; its bed time is f
+ * times its water time.  Every judge_every-th window instead runs K coupled
+ * steps and judges the prediction against them; a judged bed-change error
+ * above `bound` hands the rest to the plain solver.  *st accumulates (zero
+ * it before the first call). */
 swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwindows, int K, int f, int judge_every,
                              double bound, swe_surrogate_stats *st);
 

@@ -2,8 +2,9 @@
 
 A plain numpy restatement of the 6-layer 3x3 convolutional network that the
 tensor-core kernels run: conv3x3 with zero padding 1 written as im2col + a
-matrix product, ReLU on hidden layers, a linear output, and the backward pass
-of the mean-squared-error loss by the chain rule.  Only tests may import this
+matrix product, ReLU on hidden layers, a linear last convolution whose output
+corrects the input's linear extrapolation inside the input's activity mask,
+and the backward pass of the mean-squared-error loss by the chain rule.  Only tests may import this
 module; it shares no code with the CUDA library.
 
 Layout: images [H][W][C]; weights W[nout][9*cin] with k = tap*cin + c and
@@ -34,8 +35,10 @@ def conv3x3(X, Wm, b):
 
 def forward(X, params, round_fn=None):
     """Returns the list of layer outputs (post-activation for hidden layers)
-    and the output [H][W].  round_fn (optional) is applied to every stored
-    activation, e.g. to emulate BF16 storage."""
+    and the output [H][W] = m (z + p), z the last convolution, p and m input
+    channels 6 and 7 (the linear extrapolation and the activity mask).
+    round_fn (optional) is applied to every stored activation, e.g. to
+    emulate BF16 storage."""
     r = round_fn or (lambda a: a)
     acts = [r(X)]
     h = acts[0]
@@ -45,7 +48,7 @@ def forward(X, params, round_fn=None):
             h = r(np.maximum(z, 0.0))
             acts.append(h)
         else:
-            out = z[:, :, 0]
+            out = acts[0][:, :, 7] * (z[:, :, 0] + acts[0][:, :, 6])
     return acts, out
 
 
@@ -59,7 +62,7 @@ def loss_and_grads(X, target, params, round_fn=None):
     H, W = out.shape
     d = out - target
     loss = float(np.mean(d * d))
-    g = r((2.0 / (H * W)) * d)[:, :, None]                 # dL/d(output)
+    g = r((2.0 / (H * W)) * d * acts[0][:, :, 7])[:, :, None]   # dL/dz through out = m (z + p)
     grads = [None] * 6
     for i in range(5, -1, -1):
         Wm, b = params[i]
@@ -83,10 +86,8 @@ def random_params(seed, scale=1.0):
     rng = np.random.default_rng(seed)
     ps = []
     for i, (cin, nout) in enumerate(zip(CINS, NOUTS)):
-        fan = 9 * (4 if i == 0 else cin)
+        fan = 9 * cin
         Wm = rng.normal(0, scale * np.sqrt(2.0 / fan), (nout, 9 * cin))
-        if i == 0:
-            Wm.reshape(nout, 9, cin)[:, :, 4:] = 0.0
         b = rng.normal(0, 0.1, nout)
         ps.append((Wm, b))
     return ps

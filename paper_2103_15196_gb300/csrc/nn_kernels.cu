@@ -125,111 +125,6 @@ template <int CIN> struct ConvK {
     static constexpr int KP = (K + 15) / 16 * 16;   // padded to whole MMAs
 };
 
-// Forward (EPI_RELU: bias + ReLU -> NHWC32; EPI_OUT: channel 0 + bias -> float
-// per pixel) or input gradient (EPI_MASK: times (mask > 0) -> NHWC32).
-template <int CIN, int NOUT, int EPI>
-__global__ void __launch_bounds__(128)
-conv3x3_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
-           const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf, int H,
-           int W, int *err) {
-    constexpr int KP = ConvK<CIN>::KP;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sa = sm;                              // 128 x KP
-    unsigned char *sb = sm + 128 * KP * 2;               // NOUT x KP
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NOUT * KP * 2);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int x0 = blockIdx.x * 128, y = blockIdx.y, img = blockIdx.z;
-    const size_t plane = (size_t)H * W;
-    const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
-
-    // A: im2col of the 128-pixel segment (zero outside the image)
-    if (CIN == 32) {
-        const int cg = t & 3, pb = t >> 2;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + tap / 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp) {
-                const int p = pb + 32 * pp, xx = x0 + p + dx;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    v = *reinterpret_cast<const uint4 *>(Xi + ((size_t)yy * W + xx) * CIN + cg * 8);
-                *reinterpret_cast<uint4 *>(sa + kmajor_off(p, tap * CIN + cg * 8, 128)) = v;
-            }
-        }
-    } else {
-        const int p = t;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + tap / 3 - 1, xx = x0 + p + tap % 3 - 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                v = *reinterpret_cast<const uint4 *>(Xi + ((size_t)yy * W + xx) * CIN);
-            *reinterpret_cast<uint4 *>(sa + kmajor_off(p, tap * CIN, 128)) = v;
-        }
-        for (int k = 9 * CIN; k < KP; k += 8)
-            *reinterpret_cast<uint4 *>(sa + kmajor_off(p, k, 128)) = make_uint4(0, 0, 0, 0);
-    }
-    // B: the weights
-    for (int i = t; i < NOUT * (KP / 8); i += 128) {
-        const int r = i / (KP / 8), c = i % (KP / 8);
-        *reinterpret_cast<uint4 *>(sb + kmajor_off(r, c * 8, NOUT)) =
-            *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KP + c * 8);
-    }
-    fence_async_smem();
-    if (warp == 0) tmem_alloc(tslot, 32);
-    if (t == 0) mbar_init(mbar, 1);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    if (t == 0) {
-#pragma unroll 1
-        for (int kk = 0; kk < KP / 16; ++kk) {
-            const uint64_t ad = smem_desc(smem_u32(sa) + kk * 128 * 32, 128 * 16, 128);
-            const uint64_t bd = smem_desc(smem_u32(sb) + kk * NOUT * 32, NOUT * 16, 128);
-            mma_bf16(tmem, ad, bd, idesc_bf16_f32(NOUT), kk > 0 ? 1u : 0u);
-        }
-        mma_commit(mbar);
-    }
-    bool ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));
-    if (!ok) {
-        if (t == 0) atomicOr(err, 1);
-        ok = __syncthreads_and(mbar_wait(mbar, 0, kPolls));
-    }
-    tc_fence_after();
-    if (ok) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-        const int p = warp * 32 + lane, xx = x0 + p;
-        if (xx < W) {
-            const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
-            if (EPI == EPI_OUT) {
-                Yf[pix] = v[0] + bias[0];
-            } else {
-                __align__(16) __nv_bfloat16 o[32];
-                if (EPI == EPI_RELU) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(fmaxf(v[j] + bias[j], 0.f));
-                } else {
-                    __align__(16) __nv_bfloat16 m[32];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        reinterpret_cast<uint4 *>(m)[q] = reinterpret_cast<const uint4 *>(mask + pix * 32)[q];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(__bfloat162float(m[j]) > 0.f ? v[j] : 0.f);
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(Y + pix * 32)[q] = reinterpret_cast<uint4 *>(o)[q];
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 32);
-}
-
 // cp.async of 16 bytes into shared memory; src_bytes = 0 writes zeros.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
@@ -238,158 +133,14 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Persistent form of conv3x3_tc: one CTA per SM keeps the weights in shared
-// memory and walks 128-pixel tiles (round-robin over the grid).  Two A
-// buffers and two TMEM accumulator halves pipeline the work: while the MMAs
-// of tile i run, the CTA stores the result of tile i-1 and streams the im2col
-// of tile i+1 in with cp.async.
-template <int CIN, int NOUT, int EPI>
-__global__ void __launch_bounds__(128, 1)
-conv3x3_tcp(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
-            const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf, int H,
-            int W, int nimg, int *err) {
-    constexpr int KP = ConvK<CIN>::KP;
-    constexpr int ABYTES = 128 * KP * 2;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sa0 = sm;
-    unsigned char *sa1 = sm + ABYTES;
-    unsigned char *sb = sm + 2 * ABYTES;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NOUT * KP * 2);   // [2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int segs = (W + 127) / 128;
-    const long long ntile = (long long)nimg * H * segs;
-    const size_t plane = (size_t)H * W;
-
-    // weights, and the zero K-padding columns of both A buffers
-    for (int i = t; i < NOUT * (KP / 8); i += 128) {
-        const int r = i / (KP / 8), c = i % (KP / 8);
-        *reinterpret_cast<uint4 *>(sb + kmajor_off(r, c * 8, NOUT)) =
-            *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KP + c * 8);
-    }
-    for (int k = 9 * CIN; k < KP; k += 8) {
-        *reinterpret_cast<uint4 *>(sa0 + kmajor_off(t, k, 128)) = make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4 *>(sa1 + kmajor_off(t, k, 128)) = make_uint4(0, 0, 0, 0);
-    }
-
-    auto load_tile = [&](long long tile, unsigned char *sa) {
-        const int img = (int)(tile / ((long long)H * segs));
-        const int rem = (int)(tile % ((long long)H * segs));
-        const int y = rem / segs, x0 = (rem % segs) * 128;
-        const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
-        if (CIN == 32) {
-            const int cg = t & 3, pb = t >> 2;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int yy = y + tap / 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    const int p = pb + 32 * pp, xx = x0 + p + dx;
-                    const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                    const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN + cg * 8 : X;
-                    cp_async16(sa + kmajor_off(p, tap * CIN + cg * 8, 128), src, in ? 16 : 0);
-                }
-            }
-        } else {
-            const int p = t;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int yy = y + tap / 3 - 1, xx = x0 + p + tap % 3 - 1;
-                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN : X;
-                cp_async16(sa + kmajor_off(p, tap * CIN, 128), src, in ? 16 : 0);
-            }
-        }
-        cp_async_commit();
-    };
-
-    auto epilogue = [&](long long tile, uint32_t taddr) {
-        const int img = (int)(tile / ((long long)H * segs));
-        const int rem = (int)(tile % ((long long)H * segs));
-        const int y = rem / segs, x0 = (rem % segs) * 128;
-        float v[32];
-        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
-        const int p = warp * 32 + lane, xx = x0 + p;
-        if (xx >= W) return;
-        const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
-        if (EPI == EPI_OUT) {
-            Yf[pix] = v[0] + bias[0];
-        } else {
-            __align__(16) __nv_bfloat16 o[32];
-            if (EPI == EPI_RELU) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(fmaxf(v[j] + bias[j], 0.f));
-            } else {
-                __align__(16) __nv_bfloat16 m[32];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(m)[q] = reinterpret_cast<const uint4 *>(mask + pix * 32)[q];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) o[j] = __float2bfloat16(__bfloat162float(m[j]) > 0.f ? v[j] : 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(Y + pix * 32)[q] = reinterpret_cast<uint4 *>(o)[q];
-        }
-    };
-
-    if (warp == 0) tmem_alloc(tslot, 64);
-    if (t == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
-    long long tile = blockIdx.x;
-    if (tile < ntile) load_tile(tile, sa0);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    uint32_t ph[2] = {0, 0};
-    bool ok = true;
-    long long prev = -1;
-    int it = 0;
-    for (; tile < ntile && ok; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
-        unsigned char *sa = buf ? sa1 : sa0;
-        cp_async_wait_all();
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (t == 0) {
-#pragma unroll 1
-            for (int kk = 0; kk < KP / 16; ++kk) {
-                const uint64_t ad = smem_desc(smem_u32(sa) + kk * 128 * 32, 128 * 16, 128);
-                const uint64_t bd = smem_desc(smem_u32(sb) + kk * NOUT * 32, NOUT * 16, 128);
-                mma_bf16(tmem + buf * 32, ad, bd, idesc_bf16_f32(NOUT), kk > 0 ? 1u : 0u);
-            }
-            mma_commit(&mbar[buf]);
-        }
-        if (prev >= 0) {
-            const int pb = buf ^ 1;
-            ok = __syncthreads_and(mbar_wait(&mbar[pb], ph[pb], kPolls));
-            ph[pb] ^= 1;
-            tc_fence_after();
-            if (ok) epilogue(prev, tmem + pb * 32);
-        }
-        const long long next = tile + gridDim.x;
-        if (ok && next < ntile) load_tile(next, buf ? sa0 : sa1);
-        prev = tile;
-    }
-    if (ok && prev >= 0) {
-        const int pb = (it - 1) & 1;
-        ok = __syncthreads_and(mbar_wait(&mbar[pb], ph[pb], kPolls));
-        ph[pb] ^= 1;
-        tc_fence_after();
-        if (ok) epilogue(prev, tmem + pb * 32);
-    }
-    if (!ok) {
-        if (t == 0) atomicOr(err, 1);
-        __syncthreads_and(mbar_wait(&mbar[0], ph[0], kPolls));
-        __syncthreads_and(mbar_wait(&mbar[1], ph[1], kPolls));
-    }
-    cp_async_wait_all();
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 64);
-}
-
-// Row-streaming form of the convolution (used by the surrogate): no im2col.
+// 3x3 convolution with zero padding on the tensor cores, no im2col.  Epilogues:
+// EPI_RELU (forward, hidden layer): bias + ReLU -> NHWC32 BF16; EPI_OUT (the
+// output layer): m (channel 0 + bias + p) -> FP32 per pixel, where p and m
+// are channels 6 (the linear extrapolation of the bed change) and 7 (the
+// activity mask) of the network input, passed as `mask`; EPI_MASK (input
+// gradient): times (mask > 0) -> NHWC32 BF16.
+//
+// Row streaming:
 // A CTA owns one 128-pixel column band of an image and a run of output rows.
 // Each input row it needs is loaded once, into a shared-memory slot of 136
 // pixels (x0-1 .. x0+134) in the K-major layout, the 136 rows of each 8-channel
@@ -468,7 +219,8 @@ conv3x3_row(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict
         if (xx >= W) return;
         const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
         if (EPI == EPI_OUT) {
-            Yf[pix] = v[0] + bias[0];
+            const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * 8 + 6);
+            Yf[pix] = __high2float(pm) * (v[0] + bias[0] + __low2float(pm));
         } else {
             __align__(16) __nv_bfloat16 o[32];
             if (EPI == EPI_RELU) {
@@ -747,10 +499,12 @@ __global__ void adam_update(float *__restrict__ Wm, float *__restrict__ m, float
     }
 }
 
-// dOut = 2 (out - target) / count as channel 0 of an NHWC8 BF16 tensor;
+// dOut = 2 m (out - target) / count as channel 0 of an NHWC8 BF16 tensor
+// (m: the activity mask, channel 7 of the input X; out = m (...));
 // the squared error is summed (per block) for the loss.
-__global__ void loss_grad(const float *__restrict__ out, const float *__restrict__ target, size_t count,
-                          __nv_bfloat16 *__restrict__ dOut, float *__restrict__ loss_sum) {
+__global__ void loss_grad(const float *__restrict__ out, const float *__restrict__ target,
+                          const __nv_bfloat16 *__restrict__ X, size_t count, __nv_bfloat16 *__restrict__ dOut,
+                          float *__restrict__ loss_sum) {
     __shared__ float red[256];
     float s = 0.f;
     const float scale = 2.f / (float)count;
@@ -758,7 +512,7 @@ __global__ void loss_grad(const float *__restrict__ out, const float *__restrict
         const float d = out[i] - target[i];
         s += d * d;
         __align__(16) __nv_bfloat16 o[8];
-        o[0] = __float2bfloat16(scale * d);
+        o[0] = __float2bfloat16(__bfloat162float(X[i * 8 + 7]) * scale * d);
 #pragma unroll
         for (int j = 1; j < 8; ++j) o[j] = __float2bfloat16(0.f);
         reinterpret_cast<uint4 *>(dOut)[i] = reinterpret_cast<uint4 *>(o)[0];
@@ -778,44 +532,68 @@ __global__ void loss_grad(const float *__restrict__ out, const float *__restrict
 // (x - norm[j]) / norm[4 + j]; the cell velocity (u, v) / norm[10]; and the
 // Grass load direction of Eq. 3 with m = 2, v |v|^2, where the Shamov gate of
 // Eq. 5 is open (|v|^6 > ksh H), over norm[11].  Dry cells: zero velocity.
+constexpr int kActR = 4;   // Chebyshev radius of the activity mask
+
+__device__ __forceinline__ size_t tile_index(int x, int y, int T, int ntx) {
+    return ((size_t)(y / T) * ntx + x / T) * T * T + (size_t)(y % T) * T + x % T;
+}
+
+// Row pass of the activity mask: act[y][x] = 1 if a cell of row y within
+// kActR columns of x changed its bed since the saved bed (tile layout).
+__global__ void activity_rows(const float4 *__restrict__ state, int nx, int ny, int T, int ntx,
+                              const float *__restrict__ bsave, uint8_t *__restrict__ act) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        uint8_t a = 0;
+        for (int xx = max(0, x - kActR); xx <= min(nx - 1, x + kActR); ++xx)
+            a |= state[(size_t)y * nx + xx].w != bsave[tile_index(xx, y, T, ntx)];
+        act[i] = a;
+    }
+}
+
+// Network input tiles (channels: see the surrogate's header comment); the
+// column pass of the activity mask is done here.
 __global__ void pack_state(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ norm,
-                           float eps, float ksh, __nv_bfloat16 *__restrict__ X, size_t total) {
+                           float eps, float ksh, const float *__restrict__ bsave, const uint8_t *__restrict__ act,
+                           __nv_bfloat16 *__restrict__ X, size_t total) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t plane = (size_t)T * T;
         const int bt = (int)(i / plane);
         const int r = (int)(i % plane);
         const int y = (bt / ntx) * T + r / T, x = (bt % ntx) * T + r % T;
         __align__(16) __nv_bfloat16 o[8];
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool in = x < nx && y < ny;
-        if (in) c = state[(size_t)y * nx + x];
-        const float f[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = __float2bfloat16(in ? (f[j] - norm[j]) / norm[4 + j] : 0.f);
-        float u = 0.f, v = 0.f, jx = 0.f, jy = 0.f;
-        if (in && c.x > eps) {
-            u = c.y / c.x;
-            v = c.z / c.x;
-            const float s2 = u * u + v * v;
-            if (s2 * s2 * s2 > ksh * c.x) { jx = u * s2; jy = v * s2; }
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (x < nx && y < ny) {
+            const float4 c = state[(size_t)y * nx + x];
+            f[0] = (c.x - norm[0]) / norm[1];
+            f[1] = (c.w - norm[2]) / norm[3];
+            if (c.x > eps) {
+                const float u = c.y / c.x, v = c.z / c.x, s2 = u * u + v * v;
+                f[2] = u / norm[4];
+                f[3] = v / norm[4];
+                if (s2 * s2 * s2 > ksh * c.x) { f[4] = u * s2 / norm[5]; f[5] = v * s2 / norm[5]; }
+            }
+            f[6] = (c.w - bsave[i]) / norm[7];
+            uint8_t a = 0;
+            for (int yy = max(0, y - kActR); yy <= min(ny - 1, y + kActR); ++yy) a |= act[(size_t)yy * nx + x];
+            f[7] = a ? 1.f : 0.f;
         }
-        o[4] = __float2bfloat16(u / norm[10]);
-        o[5] = __float2bfloat16(v / norm[10]);
-        o[6] = __float2bfloat16(jx / norm[11]);
-        o[7] = __float2bfloat16(jy / norm[11]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16(f[j]);
         reinterpret_cast<uint4 *>(X)[i] = reinterpret_cast<uint4 *>(o)[0];
     }
 }
 
-// b += pred * out_std + out_mean on the solver state, for the cells of the tiles.
+// b = b_saved + pred * norm[6] on the solver state, for the cells of the tiles.
 __global__ void apply_bed(float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ pred,
-                          const float *__restrict__ norm, size_t total) {
+                          const float *__restrict__ bsave, const float *__restrict__ norm, size_t total) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t plane = (size_t)T * T;
         const int bt = (int)(i / plane);
         const int r = (int)(i % plane);
         const int y = (bt / ntx) * T + r / T, x = (bt % ntx) * T + r % T;
-        if (x < nx && y < ny) state[(size_t)y * nx + x].w += pred[i] * norm[9] + norm[8];
+        if (x < nx && y < ny) state[(size_t)y * nx + x].w = bsave[i] + pred[i] * norm[6];
     }
 }
 
@@ -844,7 +622,6 @@ struct NnLayer {
     float *grad = nullptr;   // [mt*128][noutp]
 };
 
-template <int CIN, int NOUT, int EPI> size_t conv_smem() { return (size_t)(128 + NOUT) * ConvK<CIN>::KP * 2 + 64; }
 template <int CIN, int NOUT, int DYC> size_t wgrad_smem() {
     constexpr int MT = (9 * CIN + 1 + 127) / 128;
     return (size_t)MT * 128 * 128 * 2 + (size_t)NOUT * 128 * 2 + 64;
@@ -863,7 +640,8 @@ struct swe_surrogate {
     size_t partial_floats = 0;
     long adam_t = 0;
     std::vector<void *> allocs;
-    float h_norm[12] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 1, 1, 1};
+    uint8_t *act = nullptr;
+    float h_norm[8] = {0, 1, 0, 1, 1, 1, 1, 1};
 };
 
 namespace {
@@ -876,41 +654,16 @@ cudaError_t salloc(swe_surrogate *s, void **p, size_t bytes) {
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
-int g_persist = -1;   // 1: persistent pipelined convolutions (default), 0: one CTA per tile
-
 template <int CIN, int NOUT, int EPI>
 cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, const __nv_bfloat16 *Wt, const float *bias,
                  const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B) {
-    if (g_persist < 0) {
-        // SWE_NN_CONV: 1 row-streaming (default), 2 persistent im2col, 0 one CTA per tile
-        const char *e = getenv("SWE_NN_CONV");
-        g_persist = (e && (e[0] == '0' || e[0] == '2')) ? e[0] - '0' : 1;
-    }
-    if (g_persist == 1) {
-        // row-streaming kernel
-        // at least 30 KB: at most 7 CTAs (448 TMEM columns) per SM
-        const size_t smem = std::max<size_t>(RowConv<CIN>::template smem<NOUT>(), 30 * 1024);
-        cudaFuncSetAttribute(conv3x3_row<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int rows = 16;
-        dim3 grid((s->T + 127) / 128, (s->T + rows - 1) / rows, B);
-        conv3x3_row<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
-        return cudaGetLastError();
-    }
-    if (g_persist == 2) {
-        const size_t smem = (size_t)(2 * 128 + NOUT) * ConvK<CIN>::KP * 2 + 64;
-        cudaFuncSetAttribute(conv3x3_tcp<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long ntile = (long long)B * s->T * ((s->T + 127) / 128);
-        const int grid = (int)std::min<long long>(ntile, sms);
-        conv3x3_tcp<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, B, s->err);
-        return cudaGetLastError();
-    }
-    const size_t smem = conv_smem<CIN, NOUT, EPI>();
-    cudaFuncSetAttribute(conv3x3_tc<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((s->T + 127) / 128, s->T, B);
-    conv3x3_tc<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, s->err);
+    (void)l;
+    // at least 30 KB of shared memory: at most 7 CTAs (448 TMEM columns) per SM
+    const size_t smem = std::max<size_t>(RowConv<CIN>::template smem<NOUT>(), 30 * 1024);
+    cudaFuncSetAttribute(conv3x3_row<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int rows = 16;
+    dim3 grid((s->T + 127) / 128, (s->T + rows - 1) / rows, B);
+    conv3x3_row<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
     return cudaGetLastError();
 }
 
@@ -938,7 +691,7 @@ cudaError_t forward_all(swe_surrogate *s, const __nv_bfloat16 *X, float *out, in
     cudaError_t e = conv<8, 32, EPI_RELU>(s, X, s->L[0], s->L[0].Wf, s->L[0].bias, nullptr, s->A[0], nullptr, B);
     for (int i = 1; i < 5 && e == cudaSuccess; ++i)
         e = conv<32, 32, EPI_RELU>(s, s->A[i - 1], s->L[i], s->L[i].Wf, s->L[i].bias, nullptr, s->A[i], nullptr, B);
-    if (e == cudaSuccess) e = conv<32, 16, EPI_OUT>(s, s->A[4], s->L[5], s->L[5].Wf, s->L[5].bias, nullptr, nullptr, out, B);
+    if (e == cudaSuccess) e = conv<32, 16, EPI_OUT>(s, s->A[4], s->L[5], s->L[5].Wf, s->L[5].bias, X, nullptr, out, B);
     return e;
 }
 
@@ -1018,12 +771,13 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
     if (e == cudaSuccess) e = salloc(s, (void **)&s->out, pix * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->tgt, pix * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->bsave, pix * 4);
+    if (e == cudaSuccess) e = salloc(s, (void **)&s->act, pix);
     s->partial_floats = maxpart * (size_t)max_batch * ((tile + kWgradRows - 1) / kWgradRows);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->partial, s->partial_floats * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->loss, 16);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->norm, 64);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->err, 16);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->norm, s->h_norm, 48, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->norm, s->h_norm, sizeof s->h_norm, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         swe_surrogate_destroy(s);
@@ -1033,12 +787,13 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
     return SWE_OK;
 }
 
-extern "C" swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[12]) {
+extern "C" swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[8]) {
     if (!s || !norm) return SWE_EINVAL;
-    for (int j : {4, 5, 6, 7, 9, 10, 11})
+    for (int j : {1, 3, 4, 5, 6, 7})
         if (!(norm[j] > 0)) return SWE_EINVAL;
-    std::copy(norm, norm + 12, s->h_norm);
-    if (cudaMemcpyAsync(s->norm, s->h_norm, 48, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return SWE_ECUDA;
+    std::copy(norm, norm + 8, s->h_norm);
+    if (cudaMemcpyAsync(s->norm, s->h_norm, sizeof s->h_norm, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return SWE_ECUDA;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
@@ -1056,7 +811,7 @@ extern "C" swe_status swe_surrogate_train_step(swe_surrogate *s, const void *Xv,
     cudaError_t e = forward_all(s, X, s->out, B);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, 4, s->stream);
     if (e == cudaSuccess) {
-        loss_grad<<<grid_n(pix), 256, 0, s->stream>>>(s->out, target, pix, s->dOut, s->loss);
+        loss_grad<<<grid_n(pix), 256, 0, s->stream>>>(s->out, target, X, pix, s->dOut, s->loss);
         e = cudaGetLastError();
     }
     // backward: gradient w.r.t. the pre-activations of layers 5..1, then weights
@@ -1132,29 +887,6 @@ extern "C" swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **p
 
 // ---------------------------------------------------------------- solver coupling
 
-static bool handle_state(swe_handle *h, SweConst **c, void **cur, cudaStream_t *st) {
-    SweBufs *b;
-    int prec;
-    bool set;
-    if (!swe_impl::handle_view(h, c, &b, st, nullptr, &prec, &set) || !set || prec != SWE_FP32) return false;
-    *cur = swe_impl::handle_current_state(h);
-    return *cur != nullptr;
-}
-
-extern "C" swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, int *batch) {
-    SweConst *c;
-    void *cur;
-    cudaStream_t hs;
-    if (!s || !h || !X || !handle_state(h, &c, &cur, &hs)) return SWE_EINVAL;
-    const int ntx = (c->nx + s->T - 1) / s->T, nty = (c->ny + s->T - 1) / s->T;
-    if (ntx * nty > s->maxB) return SWE_EINVAL;
-    const size_t total = (size_t)ntx * nty * s->T * s->T;
-    pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm,
-                                                     c->eps_f, c->f.ksh, (__nv_bfloat16 *)X, total);
-    if (batch) *batch = ntx * nty;
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
-}
-
 namespace {
 __global__ void bed_tiles(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, float *__restrict__ b,
                           size_t total) {
@@ -1168,123 +900,159 @@ __global__ void bed_tiles(const float4 *__restrict__ state, int nx, int ny, int 
 __global__ void make_target(const float *__restrict__ b0, const float *__restrict__ b1, const float *__restrict__ norm,
                             float *__restrict__ out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = ((b1[i] - b0[i]) - norm[8]) / norm[9];
-}
-}  // namespace
-
-// Target of a sample: the handle's bed now minus the bed saved by the last
-// swe_surrogate_save_bed call, normalised, in the tile layout (device out).
-extern "C" swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h) {
-    SweConst *c;
-    void *cur;
-    cudaStream_t hs;
-    if (!s || !h || !handle_state(h, &c, &cur, &hs)) return SWE_EINVAL;
-    const int ntx = (c->nx + s->T - 1) / s->T, nty = (c->ny + s->T - 1) / s->T;
-    if (ntx * nty > s->maxB) return SWE_EINVAL;
-    const size_t total = (size_t)ntx * nty * s->T * s->T;
-    bed_tiles<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->bsave, total);
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+        out[i] = (b1[i] - b0[i]) / norm[6];
 }
 
-extern "C" swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target) {
-    SweConst *c;
-    void *cur;
-    cudaStream_t hs;
-    if (!s || !h || !target || !handle_state(h, &c, &cur, &hs)) return SWE_EINVAL;
-    const int ntx = (c->nx + s->T - 1) / s->T, nty = (c->ny + s->T - 1) / s->T;
-    const size_t total = (size_t)ntx * nty * s->T * s->T;
-    bed_tiles<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->tgt, total);
-    make_target<<<grid_n(total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->norm, target, total);
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
-}
-
-// Predicts the bed change of one window from the handle's current state and
-// adds it to the bed (b += pred * std + mean) in place.
-extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
-    SweConst *c;
-    void *cur;
-    cudaStream_t hs;
-    if (!s || !h || !handle_state(h, &c, &cur, &hs)) return SWE_EINVAL;
-    const int ntx = (c->nx + s->T - 1) / s->T, nty = (c->ny + s->T - 1) / s->T;
-    if (ntx * nty > s->maxB) return SWE_EINVAL;
-    const int B = ntx * nty;
-    const size_t total = (size_t)B * s->T * s->T;
-    pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
-                                                     c->f.ksh, s->X0, total);
-    if (forward_all(s, s->X0, s->out, B) != cudaSuccess) return SWE_ECUDA;
-    apply_bed<<<grid_n(total), 256, 0, s->stream>>>((float4 *)cur, c->nx, c->ny, s->T, ntx, s->out, s->norm, total);
-    if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
-    swe_status st = check_err(s);
-    if (st == SWE_OK) st = (swe_status)swe_impl::handle_state_changed(h);
-    return st;
-}
-
-namespace {
-// Judged-window error sums (FP64): |b0 + pred - b1|, |b1 - b0|, |b1|,
-// |last - (b1 - b0)| over the cells of the domain.
+// Judged-window error sums (FP64) over the cells of the domain, ch = b1 - b0
+// the plain solver's bed change:  |pred - ch|, |ch|, |b1|, |last - ch|,
+// |p - ch| (p: input channel 6, the linear extrapolation).
 __global__ void judge_sums(const float *__restrict__ b0, const float *__restrict__ b1, const float *__restrict__ pred,
-                           const float *__restrict__ last, const float *__restrict__ norm, int nx, int ny, int T, int ntx,
-                           size_t total, double *__restrict__ out) {
-    __shared__ double red[4][256];
-    double a = 0, b = 0, c = 0, d = 0;
+                           const float *__restrict__ last, const __nv_bfloat16 *__restrict__ X,
+                           const float *__restrict__ norm, int nx, int ny, int T, int ntx, size_t total,
+                           double *__restrict__ out) {
+    __shared__ double red[5][256];
+    double q[5] = {0, 0, 0, 0, 0};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t plane = (size_t)T * T;
         const int bt = (int)(i / plane), r = (int)(i % plane);
         const int y = (bt / ntx) * T + r / T, x = (bt % ntx) * T + r % T;
         if (x >= nx || y >= ny) continue;
         const double ch = (double)b1[i] - (double)b0[i];
-        const double pr = (double)pred[i] * norm[9] + norm[8];
-        a += fabs(pr - ch);
-        b += fabs(ch);
-        c += fabs((double)b1[i]);
-        d += fabs((double)last[i] - ch);
+        q[0] += fabs((double)pred[i] * norm[6] - ch);
+        q[1] += fabs(ch);
+        q[2] += fabs((double)b1[i]);
+        q[3] += fabs((double)last[i] - ch);
+        q[4] += fabs((double)__bfloat162float(X[i * 8 + 6]) * norm[6] - ch);
     }
-    red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c; red[3][threadIdx.x] = d;
+    for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = q[k];
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
-            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+            for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int q = 0; q < 4; ++q) atomicAdd(&out[q], red[q][0]);
+        for (int k = 0; k < 5; ++k) atomicAdd(&out[k], red[k][0]);
 }
 __global__ void diff_into(const float *__restrict__ b0, const float *__restrict__ b1, float *__restrict__ d, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         d[i] = b1[i] - b0[i];
 }
+
+// The handle as the surrogate sees it: its FP32 state, tile grid and stream.
+struct Coupling {
+    SweConst *c = nullptr;
+    void *cur = nullptr;
+    cudaStream_t hs = nullptr;
+    int ntx = 0, nty = 0;
+    size_t total = 0;
+};
+
+bool couple(swe_surrogate *s, swe_handle *h, Coupling &k) {
+    SweBufs *b;
+    int prec;
+    bool set;
+    if (!s || !h || !swe_impl::handle_view(h, &k.c, &b, &k.hs, nullptr, &prec, &set) || !set || prec != SWE_FP32)
+        return false;
+    k.cur = swe_impl::handle_current_state(h);
+    k.ntx = (k.c->nx + s->T - 1) / s->T;
+    k.nty = (k.c->ny + s->T - 1) / s->T;
+    k.total = (size_t)k.ntx * k.nty * s->T * s->T;
+    return k.cur != nullptr && k.ntx * k.nty <= s->maxB;
+}
+
+// Orders the surrogate's stream after the solver's work so far.
+swe_status after_solver(swe_surrogate *s, const Coupling &k) {
+    if (k.hs == s->stream) return SWE_OK;
+    return cudaStreamSynchronize(k.hs) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
+void launch_save(swe_surrogate *s, const Coupling &k, float *dst) {
+    bed_tiles<<<grid_n(k.total), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, dst, k.total);
+}
+
+void launch_pack(swe_surrogate *s, const Coupling &k, __nv_bfloat16 *X) {
+    const size_t n = (size_t)k.c->nx * k.c->ny;
+    activity_rows<<<grid_n(n), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->bsave, s->act);
+    pack_state<<<grid_n(k.total), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->norm,
+                                                       k.c->eps_f, k.c->f.ksh, s->bsave, s->act, X, k.total);
+}
+
+// Sets the bed to saved + prediction (s->out) and lets the handle re-form
+// its census and dt for the new bed.
+swe_status launch_apply(swe_surrogate *s, swe_handle *h, const Coupling &k) {
+    apply_bed<<<grid_n(k.total), 256, 0, s->stream>>>((float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->out, s->bsave,
+                                                      s->norm, k.total);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) return SWE_ECUDA;
+    return (swe_status)swe_impl::handle_state_changed(h);
+}
 }  // namespace
 
-// Surrogate-accelerated run (morphological acceleration, a project addition):
-// each window stands for K coupled steps of the bed.  In a surrogate window
-// the network predicts the window's bed change from the window's start state,
-// the water alone is advanced K/f steps (Exner coupling off), and the
-// prediction is added to the bed: the bed's simulated time advances f times
-// faster than the water's.  Every judge_every-th window is judged instead:
-// the plain coupled solver runs the K steps from the same start state, the
-// relative L1 error of the predicted bed change against it is recorded (and,
-// for reference, that of a zero change and of repeating the last judged
-// change), and the run continues from the plain result.  A judged error above
-// `bound` hands every remaining window to the plain solver.
+extern "C" swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, int *batch) {
+    Coupling k;
+    if (!X || !couple(s, h, k)) return SWE_EINVAL;
+    swe_status st = after_solver(s, k);
+    if (st != SWE_OK) return st;
+    launch_pack(s, k, (__nv_bfloat16 *)X);
+    if (batch) *batch = k.ntx * k.nty;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
+extern "C" swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h) {
+    Coupling k;
+    if (!couple(s, h, k)) return SWE_EINVAL;
+    swe_status st = after_solver(s, k);
+    if (st != SWE_OK) return st;
+    launch_save(s, k, s->bsave);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
+extern "C" swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target) {
+    Coupling k;
+    if (!target || !couple(s, h, k)) return SWE_EINVAL;
+    swe_status st = after_solver(s, k);
+    if (st != SWE_OK) return st;
+    launch_save(s, k, s->tgt);
+    make_target<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->norm, target, k.total);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
+extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
+    Coupling k;
+    if (!couple(s, h, k)) return SWE_EINVAL;
+    swe_status st = after_solver(s, k);
+    if (st != SWE_OK) return st;
+    launch_pack(s, k, s->X0);
+    if (forward_all(s, s->X0, s->out, k.ntx * k.nty) != cudaSuccess) return SWE_ECUDA;
+    if ((st = check_err(s)) != SWE_OK) return st;
+    return launch_apply(s, h, k);
+}
+
 extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwindows, int K, int f, int judge_every,
                                        double bound, swe_surrogate_stats *st) {
-    SweConst *c;
-    void *cur;
-    cudaStream_t hs;
-    if (!s || !h || !st || nwindows < 0 || K < 1 || f < 1 || (K % f) || judge_every < 1 || !(bound > 0) ||
-        !handle_state(h, &c, &cur, &hs))
+    Coupling k;
+    if (!st || nwindows < 0 || K < 2 || f < 1 || (K % f) || judge_every < 1 || !(bound > 0) || !couple(s, h, k))
         return SWE_EINVAL;
-    const int ntx = (c->nx + s->T - 1) / s->T, nty = (c->ny + s->T - 1) / s->T;
-    const int B = ntx * nty;
-    if (B > s->maxB) return SWE_EINVAL;
-    const size_t total = (size_t)B * s->T * s->T;
+    const int B = k.ntx * k.nty;
     double *dsum = nullptr;
     float *last = nullptr;
-    if (cudaMalloc(&dsum, 4 * sizeof(double)) != cudaSuccess) return SWE_ENOMEM;
-    if (cudaMalloc(&last, total * 4) != cudaSuccess) { cudaFree(dsum); return SWE_ENOMEM; }
-    cudaMemsetAsync(last, 0, total * 4, s->stream);
-    double err_sum = 0, zero_sum = 0, pers_sum = 0;
+    if (cudaMalloc(&dsum, 5 * sizeof(double)) != cudaSuccess) return SWE_ENOMEM;
+    if (cudaMalloc(&last, k.total * 4) != cudaSuccess) { cudaFree(dsum); return SWE_ENOMEM; }
+    cudaMemsetAsync(last, 0, k.total * 4, s->stream);
+    double err_sum = 0, zero_sum = 0, pers_sum = 0, lin_sum = 0;
     swe_status rc = SWE_OK;
+    // the network's prediction from the state one coupled step into the window
+    auto first_step_and_predict = [&]() -> swe_status {
+        swe_status r;
+        if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
+        launch_save(s, k, s->bsave);
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SWE_ECUDA;
+        if ((r = swe_run_steps(h, 1)) != SWE_OK) return r;
+        if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
+        launch_pack(s, k, s->X0);
+        if (forward_all(s, s->X0, s->out, B) != cudaSuccess) return SWE_ECUDA;
+        return check_err(s);
+    };
     for (int w = 0; w < nwindows && rc == SWE_OK; ++w) {
         double t0 = 0, t1 = 0;
         if ((rc = swe_get_time(h, &t0)) != SWE_OK) break;
@@ -1293,59 +1061,54 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             st->bed_time += t1 - t0;
             st->water_time += t1 - t0;
             ++st->plain_windows;
-        } else if (w % judge_every == 0) {                       // judged window
-            handle_state(h, &c, &cur, &hs);
-            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
-                                                     c->f.ksh, s->X0, total);
-            bed_tiles<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->bsave, total);
-            if (forward_all(s, s->X0, s->out, B) != cudaSuccess) { rc = SWE_ECUDA; break; }
-            if ((rc = check_err(s)) != SWE_OK) break;
-            if ((rc = swe_run_steps(h, K)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
-            handle_state(h, &c, &cur, &hs);
-            bed_tiles<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->tgt, total);
-            cudaMemsetAsync(dsum, 0, 4 * sizeof(double), s->stream);
-            judge_sums<<<grid_n(total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->out, last, s->norm, c->nx, c->ny,
-                                                            s->T, ntx, total, dsum);
-            diff_into<<<grid_n(total), 256, 0, s->stream>>>(s->bsave, s->tgt, last, total);
-            double hsum[4];
-            if (cudaMemcpyAsync(hsum, dsum, sizeof hsum, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        } else if (w % judge_every == 0) {                       // judged window: K coupled steps
+            if ((rc = first_step_and_predict()) != SWE_OK) break;
+            if ((rc = swe_run_steps(h, K - 1)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
+            if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
+            launch_save(s, k, s->tgt);
+            cudaMemsetAsync(dsum, 0, 5 * sizeof(double), s->stream);
+            judge_sums<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->out, last, s->X0, s->norm, k.c->nx,
+                                                              k.c->ny, s->T, k.ntx, k.total, dsum);
+            diff_into<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, last, k.total);
+            double q[5];
+            if (cudaMemcpyAsync(q, dsum, sizeof q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
                 cudaStreamSynchronize(s->stream) != cudaSuccess) { rc = SWE_ECUDA; break; }
-            const double ref = hsum[1] > 0 ? hsum[1] : 1e-300;
-            const double err = hsum[0] / ref;
+            const double ref = q[1] > 0 ? q[1] : 1e-300;
+            const double err = q[0] / ref;
             st->err_last = err;
             st->err_max = std::max(st->err_max, err);
-            st->elev_err_max = std::max(st->elev_err_max, hsum[0] / (hsum[2] > 0 ? hsum[2] : 1e-300));
+            st->elev_err_max = std::max(st->elev_err_max, q[0] / (q[2] > 0 ? q[2] : 1e-300));
             err_sum += err;
             zero_sum += 1.0;
-            pers_sum += hsum[3] / ref;
+            pers_sum += q[3] / ref;
+            lin_sum += q[4] / ref;
             ++st->judged;
             st->err_mean = err_sum / st->judged;
             st->err_zero_mean = zero_sum / st->judged;
             st->err_persist_mean = pers_sum / st->judged;
+            st->err_linear_mean = lin_sum / st->judged;
             st->bed_time += t1 - t0;
             st->water_time += t1 - t0;
             if (err > bound) { st->mode = 1; st->takeover_window = w; }
         } else {                                                 // surrogate window
-            handle_state(h, &c, &cur, &hs);
-            pack_state<<<grid_n(total), 256, 0, s->stream>>>((const float4 *)cur, c->nx, c->ny, s->T, ntx, s->norm, c->eps_f,
-                                                     c->f.ksh, s->X0, total);
-            if (forward_all(s, s->X0, s->out, B) != cudaSuccess) { rc = SWE_ECUDA; break; }
-            if ((rc = check_err(s)) != SWE_OK) break;
-            if ((rc = swe_set_sediment(h, 0)) != SWE_OK) break;
-            rc = swe_run_steps(h, K / f);
-            swe_status r2 = swe_set_sediment(h, 1);
-            if (rc == SWE_OK) rc = r2;
-            if (rc != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
-            handle_state(h, &c, &cur, &hs);
-            apply_bed<<<grid_n(total), 256, 0, s->stream>>>((float4 *)cur, c->nx, c->ny, s->T, ntx, s->out, s->norm, total);
-            if (cudaStreamSynchronize(s->stream) != cudaSuccess) { rc = SWE_ECUDA; break; }
-            rc = (swe_status)swe_impl::handle_state_changed(h);
+            if ((rc = first_step_and_predict()) != SWE_OK) break;
+            if (K / f > 1) {
+                if ((rc = swe_set_sediment(h, 0)) != SWE_OK) break;
+                rc = swe_run_steps(h, K / f - 1);
+                const swe_status r2 = swe_set_sediment(h, 1);
+                if (rc == SWE_OK) rc = r2;
+                if (rc != SWE_OK) break;
+            }
+            if ((rc = swe_get_time(h, &t1)) != SWE_OK) break;
+            if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
+            if ((rc = launch_apply(s, h, k)) != SWE_OK) break;
             st->bed_time += (t1 - t0) * f;
             st->water_time += t1 - t0;
             ++st->surrogate_windows;
         }
         ++st->windows;
     }
+    cudaStreamSynchronize(s->stream);
     cudaFree(dsum);
     cudaFree(last);
     return rc;

@@ -64,7 +64,7 @@ class SurrogateStats(ctypes.Structure):
         ("bed_time", ctypes.c_double), ("water_time", ctypes.c_double),
         ("err_last", ctypes.c_double), ("err_max", ctypes.c_double), ("err_mean", ctypes.c_double),
         ("err_zero_mean", ctypes.c_double), ("err_persist_mean", ctypes.c_double),
-        ("elev_err_max", ctypes.c_double), ("mode", ctypes.c_int),
+        ("err_linear_mean", ctypes.c_double), ("elev_err_max", ctypes.c_double), ("mode", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -407,7 +407,10 @@ class Surrogate:
         return ctypes.c_void_p(t.data_ptr())
 
     def set_norm(self, norm):
-        a = (ctypes.c_float * 12)(*[float(x) for x in norm])
+        """norm: H mean, H std, b mean, b std, velocity scale, transport
+        scale, output unit (m of bed change), first-step scale (unit / K)."""
+        assert len(norm) == 8
+        a = (ctypes.c_float * 8)(*[float(x) for x in norm])
         self._check(self._L.swe_surrogate_set_norm(self._h, a))
 
     def forward(self, X, out, B):

@@ -1,6 +1,7 @@
 """Pins of the CPU reference network (oracle/cnn_oracle.py): the convolution
-against scipy's 2D correlation, and the back-propagated gradients against
-central finite differences of the loss."""
+against scipy's 2D correlation, the output's reduction to the masked linear
+extrapolation when the last convolution is zero, and the back-propagated
+gradients against central finite differences of the loss."""
 import numpy as np
 import pytest
 
@@ -22,11 +23,30 @@ def test_conv3x3_matches_scipy_correlate2d():
         assert np.allclose(Y[:, :, n], ref, atol=1e-12)
 
 
+def _features(rng, H, W):
+    X = rng.normal(size=(H, W, 8))
+    X[:, :, 7] = rng.random((H, W)) < 0.7          # activity mask
+    return X
+
+
+def test_zero_last_layer_gives_masked_linear_extrapolation():
+    rng = np.random.default_rng(3)
+    X = _features(rng, 5, 7)
+    params = C.random_params(4)
+    params[5] = (0 * params[5][0], 0 * params[5][1])
+    _, out = C.forward(X, params)
+    assert np.array_equal(out, np.where(X[:, :, 7] > 0, X[:, :, 6], 0.0))
+    # no gradient reaches the network where the mask is off
+    Xm = X.copy()
+    Xm[:, :, 7] = 0
+    _, grads, out = C.loss_and_grads(Xm, rng.normal(size=(5, 7)), C.random_params(4))
+    assert not out.any() and all(not g.any() and not b.any() for g, b in grads)
+
+
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(1)
     H = W = 6
-    X = np.zeros((H, W, 8))
-    X[:, :, :4] = rng.normal(size=(H, W, 4))
+    X = _features(rng, H, W)
     target = rng.normal(size=(H, W))
     params = C.random_params(2)
     loss, grads, _ = C.loss_and_grads(X, target, params)
@@ -36,8 +56,6 @@ def test_gradients_match_finite_differences():
         for _ in range(6):
             n = rng.integers(Wm.shape[0])
             k = rng.integers(Wm.shape[1])
-            if layer == 0 and k % 8 >= 4:
-                continue
             old = Wm[n, k]
             Wm[n, k] = old + eps
             lp = C.loss_and_grads(X, target, params)[0]

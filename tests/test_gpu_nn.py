@@ -59,8 +59,8 @@ def _setup(seed, T=128, out_scale=1.0):
     # what the kernels see: BF16 weights, FP32 biases
     used = [(_bf16_round(Wm), np.asarray(b, np.float32).astype(np.float64)) for Wm, b in params]
     rng = np.random.default_rng(seed + 10)
-    X = np.zeros((T, T, 8))
-    X[:, :, :4] = rng.normal(size=(T, T, 4))
+    X = rng.normal(size=(T, T, 8))
+    X[:, :, 7] = rng.random((T, T)) < 0.7          # activity mask
     Xb = _bf16_round(X)
     Xd = torch.from_numpy(Xb.astype(np.float32)).to(torch.bfloat16).cuda().contiguous()
     return S, used, Xb, Xd
@@ -96,9 +96,6 @@ def test_surrogate_gradients_match_cpu_reference(lib):
     for layer in range(6):
         gW, gb = S.grads(layer)
         rW, rb = ref_grads[layer]
-        if layer == 0:
-            keep = (np.arange(rW.shape[1]) % 8) < 4
-            gW, rW = gW[:, keep], rW[:, keep]
         eW = np.linalg.norm(gW - rW) / np.linalg.norm(rW)
         eb = np.linalg.norm(gb - rb) / max(np.linalg.norm(rb), 1e-30)
         assert eW < 5e-2 and eb < 5e-2, (layer, eW, eb)
@@ -106,13 +103,15 @@ def test_surrogate_gradients_match_cpu_reference(lib):
 
 
 def test_surrogate_training_reduces_loss(lib):
-    """A smooth target the network can express (a blur of the bed channel):
-    Adam on the tensor-core kernels must drive the loss down."""
+    """A target the network can express (the masked linear extrapolation
+    plus a blur of the bed channel): Adam on the tensor-core kernels must
+    drive the loss down."""
     import torch
     T = 128
     S, used, Xb, Xd = _setup(5, T)
-    b = Xb[:, :, 3]
-    tgt = 0.25 * (np.roll(b, 1, 0) + np.roll(b, -1, 0) + np.roll(b, 1, 1) + np.roll(b, -1, 1))
+    b = Xb[:, :, 1]
+    blur = 0.25 * (np.roll(b, 1, 0) + np.roll(b, -1, 0) + np.roll(b, 1, 1) + np.roll(b, -1, 1))
+    tgt = Xb[:, :, 7] * (Xb[:, :, 6] + blur)
     td = torch.from_numpy(tgt.astype(np.float32)).cuda()[None].contiguous()
     losses = [S.train_step(Xd, td, 1, 2e-3) for _ in range(150)]
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
@@ -120,11 +119,13 @@ def test_surrogate_training_reduces_loss(lib):
 
 
 def _solver_case(swe, I):
+    """A 256^2 flood scenario, spun up 60 steps so that sediment moves."""
     sc = I.ensemble_scenario(256, seed=901, manning=0.03, peak=300.0, d50_scale=1.0)
     Sv = swe.Solver(256, 256, 5.0, precision="fp32", A_J=0.01)
     Sv.set_manning(sc.manning, block=sc.manning_block)
     Sv.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
     Sv.set_state(sc.H, sc.Hu, sc.Hv, sc.b)
+    Sv.run_steps(60)
     return sc, Sv
 
 
@@ -151,18 +152,33 @@ def test_surrogate_takeover_with_a_bad_network(lib):
 
 
 def test_surrogate_windows_advance_the_bed_faster(lib):
-    """A network predicting exactly no change: judged error 1 (what 'no
-    change' scores), surrogate windows advance the water K/f steps and the
-    bed time f times as far, and leave the bed untouched."""
+    """A network whose last convolution is zero predicts the masked linear
+    extrapolation of the window's first step: its judged error is the
+    linear ablation's, surrogate windows advance the water K/f steps and
+    the bed time f times as far, and set the bed to the window-start bed
+    plus the first step's change times K."""
+    import torch
     from paper_2103_15196_gb300 import inputs as I
     from paper_2103_15196_gb300 import swe
+    K, f = 20, 5
     sc, Sv = _solver_case(swe, I)
     S = swe.Surrogate(tile=128, max_batch=4, seed=9)
-    for i in range(6):
-        Wm, b = S.params(i)
-        S.set_params(i, 0 * Wm, 0 * b)
-    st = S.run(Sv, nwindows=3, K=20, f=5, judge_every=3, bound=2.0)
+    S.set_norm([0.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1e-3, 1e-3 / K])
+    Wm, b = S.params(5)
+    S.set_params(5, 0 * Wm, 0 * b)
+    st = S.run(Sv, nwindows=3, K=K, f=f, judge_every=3, bound=2.0)
     assert st.judged == 1 and st.surrogate_windows == 2 and st.mode == 0
-    assert st.err_last == pytest.approx(1.0, abs=1e-12)
+    assert 0 < st.err_last < 1.0
+    assert st.err_last == pytest.approx(st.err_linear_mean, rel=1e-12)
     assert st.bed_time > 1.8 * st.water_time
+    # one more surrogate window by hand: save, one coupled step, apply
+    b0 = Sv.get_state(np.float32)[3].astype(np.float64)
+    S.save_bed(Sv)
+    Sv.run_steps(1)
+    b1 = Sv.get_state(np.float32)[3].astype(np.float64)
+    S.apply(Sv)
+    got = Sv.get_state(np.float32)[3].astype(np.float64)
+    p = torch.tensor((b1 - b0) / (1e-3 / K)).to(torch.bfloat16).double().numpy()
+    want = (b0 + p * 1e-3).astype(np.float32)
+    assert np.allclose(got, want, rtol=0, atol=1e-6 * max(1.0, np.abs(b0).max()))
     S.close()
