@@ -234,7 +234,7 @@ def run_reference(args):
 
 
 def run_ensemble(args, torch, swe):
-    """Config 4: 64 flood scenarios, sides 32*U{8..64} (256..2048), per-scenario
+    """The batched ensemble: 64 flood scenarios, sides 32*U{8..64} (256..2048), per-scenario
     terrain seed, Manning n ~ U[0.02, 0.06], inflow peak ~ U[50, 1000] m^3/s,
     d50 scale ~ U[0.5, 2]; one persistent launch per run, autotuned blocks.
     Returns aggregate Gcell/s and the same scenarios run one after another."""
@@ -288,7 +288,7 @@ def run_ensemble(args, torch, swe):
 
 
 def run_surrogate(args, torch, swe):
-    """Config 5: the learned bed surrogate.  2000 samples (500 snapshots x 4
+    """The learned bed surrogate.  2000 samples (500 snapshots x 4
     tiles of 1024^2) of (state, bed change over K = 50 steps) from solver runs
     on the 2048^2 flood-channel terrain class (fractal DEM + carved channel,
     half wet with a dam-break step, inflow hydrograph), training on the GPU,
@@ -325,39 +325,86 @@ def run_surrogate(args, torch, swe):
     sv.close()
     net = swe.Surrogate(tile=T, max_batch=4, seed=0, stream=sp)
     net.set_norm(norm)
+    net.set_loss(args.sur_loss)
     nsnap = args.sur_samples // 4
     X = torch.empty((nsnap * 4, T, T, 8), dtype=torch.bfloat16, device="cuda")
     Y = torch.empty((nsnap * 4, T, T), dtype=torch.float32, device="cuda")
     nscen = max(1, nsnap // args.sur_snaps_per_run)
-    k = 0
-    for r in range(nscen):
-        sv = solver(scenario(7100 + r))
+
+    def sample_run(seed, Xs, Ys, count, k0):
+        """count windows of one scenario, a skipped window between samples:
+        its start bed, one coupled step (the network's input state), then
+        the rest of the K coupled steps (the target)."""
+        sv = solver(scenario(seed))
         sv.run_steps(args.sur_spin)
-        for _ in range(nsnap // nscen if r < nscen - 1 else nsnap - k):
-            # a window: its start bed, one coupled step (the network's input
-            # state), then the rest of the K coupled steps (the target)
+        for j in range(count):
             net.save_bed(sv)
             sv.run_steps(1)
-            net.pack_state(sv, X[4 * k:4 * k + 4])
+            net.pack_state(sv, Xs[4 * (k0 + j):4 * (k0 + j) + 4])
             sv.run_steps(K - 1)
-            net.pack_target(sv, Y[4 * k:4 * k + 4])
-            k += 1
+            net.pack_target(sv, Ys[4 * (k0 + j):4 * (k0 + j) + 4])
+            sv.run_steps(K * args.sur_gap)
         sv.close()
+
+    k = 0
+    for r in range(nscen):
+        cnt = nsnap // nscen if r < nscen - 1 else nsnap - k
+        sample_run(7100 + r, X, Y, cnt, k)
+        k += cnt
+    nval = args.sur_val // 4
+    Xv = torch.empty((nval * 4, T, T, 8), dtype=torch.bfloat16, device="cuda")
+    Yv = torch.empty((nval * 4, T, T), dtype=torch.float32, device="cuda")
+    sample_run(7500, Xv, Yv, nval, 0)
+    ov = torch.empty((4, T, T), dtype=torch.float32, device="cuda")
+
+    def validate():
+        """Relative L1 of the network and of the linear extrapolation alone
+        on held-out windows (output units)."""
+        e_net = e_lin = ref = 0.0
+        for j in range(nval):
+            net.forward(Xv[4 * j:4 * j + 4], ov, 4)
+            torch.cuda.synchronize()
+            o = ov.cpu().numpy().astype(np.float64)
+            y = Yv[4 * j:4 * j + 4].cpu().numpy().astype(np.float64)
+            xs = Xv[4 * j:4 * j + 4, :, :, 6:8].float().cpu().numpy().astype(np.float64)
+            e_net += np.abs(o - y).sum()
+            e_lin += np.abs(xs[..., 0] * xs[..., 1] - y).sum()
+            ref += np.abs(y).sum()
+        return e_net / ref, e_lin / ref
+
     t_data = time.perf_counter() - t_all
     # training
     t0 = time.perf_counter()
     g = torch.Generator().manual_seed(0)
     steps, first, last = 0, None, None
     lr0 = args.sur_lr
+    val_curve = []
+    v_net, v_lin = validate()
+    best = (v_net, [net.params(i) for i in range(6)])
+    val_curve.append((0, v_net))
+    next_val = args.sur_train_seconds / args.sur_val_points
     while time.perf_counter() - t0 < args.sur_train_seconds:
         for i in torch.randperm(nsnap, generator=g).tolist():
-            frac = min(1.0, (time.perf_counter() - t0) / args.sur_train_seconds)
+            el = time.perf_counter() - t0
+            frac = min(1.0, el / args.sur_train_seconds)
             loss = net.train_step(X[4 * i:4 * i + 4], Y[4 * i:4 * i + 4], 4, lr0 * (0.1 + 0.9 * (1 - frac)))
             first = loss if first is None else first
             last = loss
             steps += 1
+            if el >= next_val:
+                next_val += args.sur_train_seconds / args.sur_val_points
+                vn, _ = validate()
+                val_curve.append((steps, vn))
+                if vn < best[0]:
+                    best = (vn, [net.params(j) for j in range(6)])
             if time.perf_counter() - t0 >= args.sur_train_seconds:
                 break
+    vn, _ = validate()
+    val_curve.append((steps, vn))
+    if vn < best[0]:
+        best = (vn, [net.params(j) for j in range(6)])
+    for j, (Wm, b_) in enumerate(best[1]):
+        net.set_params(j, Wm, b_)
     t_train = time.perf_counter() - t0
     # forward time of one 2048^2 domain (4 tiles)
     outb = torch.empty((4, T, T), dtype=torch.float32, device="cuda")
@@ -369,7 +416,7 @@ def run_surrogate(args, torch, swe):
     fb.record(stream)
     fb.synchronize()
     fwd_ms = fa.elapsed_time(fb) / 5
-    del X, Y, outb
+    del X, Y, outb, Xv, Yv, ov
     torch.cuda.empty_cache()
     # evaluation on an unseen scenario: plain coupled method vs surrogate windows
     sc = scenario(7999)
@@ -386,20 +433,35 @@ def run_surrogate(args, torch, swe):
     wall_p = e0.elapsed_time(e1) * 1e-3
     bed_p = A.t - ta
     A.close()
-    Bs = solver(sc)
-    Bs.run_steps(args.sur_spin)
-    Bs.sync()
-    w0 = time.perf_counter()
-    st = net.run(Bs, R, K=K, f=f, judge_every=J, bound=args.sur_bound)
-    wall_s = time.perf_counter() - w0
-    Bs.close()
-    net.close()
     rate_p = bed_p / wall_p
+
+    def surrogate_run(f_, J_):
+        Bs = solver(sc)
+        Bs.run_steps(args.sur_spin)
+        Bs.sync()
+        w0 = time.perf_counter()
+        st_ = net.run(Bs, R, K=K, f=f_, judge_every=J_, bound=args.sur_bound)
+        wall = time.perf_counter() - w0
+        Bs.close()
+        return st_, wall
+
+    st, wall_s = surrogate_run(f, J)
     rate_s = st.bed_time / wall_s
+    variants = []
+    for v in filter(None, args.sur_variants.split(",")):
+        fv, jv = (int(x) for x in v.split(":"))
+        sv_, wv = surrogate_run(fv, jv)
+        variants.append({"f": fv, "judge_every": jv, "speedup": sv_.bed_time / wv / rate_p,
+                         "err_mean": sv_.err_mean, "err_max": sv_.err_max, "err_linear_mean": sv_.err_linear_mean,
+                         "elev_err_max": sv_.elev_err_max, "mode": sv_.mode})
+    net.close()
     out = {"metric": "surrogate bed simulated-time rate / plain method's, at judged error",
            "speedup": rate_s / rate_p, "rate_plain_s_per_s": rate_p, "rate_surrogate_s_per_s": rate_s,
-           "K": K, "f": f, "judge_every": J, "bound": args.sur_bound, "windows": R,
-           "stats": st.as_dict(), "train_steps": steps, "train_loss_first": first, "train_loss_last": last,
+           "K": K, "f": f, "judge_every": J, "loss": args.sur_loss, "lr": args.sur_lr, "bound": args.sur_bound, "windows": R,
+           "stats": st.as_dict(), "variants": variants,
+           "validation": {"samples": nval * 4, "err_linear": v_lin, "err_network_best": best[0],
+                          "curve": val_curve},
+           "train_steps": steps, "train_loss_first": first, "train_loss_last": last,
            "samples": nsnap * 4, "tile": T, "forward_ms_2048sq": fwd_ms,
            "plain_window_ms": wall_p * 1e3 / R,
            "seconds": {"data": t_data, "train": t_train, "eval": wall_p + wall_s},
@@ -556,14 +618,20 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-only", action="store_true", help="run only the config-5 surrogate experiment")
     ap.add_argument("--sur-samples", type=int, default=2000)
-    ap.add_argument("--sur-snaps-per-run", type=int, default=100)
+    ap.add_argument("--sur-snaps-per-run", type=int, default=25)
     ap.add_argument("--sur-spin", type=int, default=300)
-    ap.add_argument("--sur-train-seconds", type=float, default=60.0)
+    ap.add_argument("--sur-train-seconds", type=float, default=30.0)
     ap.add_argument("--sur-lr", type=float, default=1e-3)
     ap.add_argument("--sur-windows", type=int, default=40)
     ap.add_argument("--sur-f", type=int, default=10)
     ap.add_argument("--sur-judge", type=int, default=10)
     ap.add_argument("--sur-bound", type=float, default=0.5)
+    ap.add_argument("--sur-loss", default="l1", choices=["mse", "l1"])
+    ap.add_argument("--sur-gap", type=int, default=1, help="windows skipped between training samples")
+    ap.add_argument("--sur-val", type=int, default=80, help="held-out validation samples (tiles)")
+    ap.add_argument("--sur-val-points", type=int, default=6)
+    ap.add_argument("--sur-variants", default="10:20,25:20,50:20",
+                    help="extra f:judge_every evaluations of the trained network")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

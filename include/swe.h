@@ -262,8 +262,8 @@ swe_status swe_set_sediment(swe_handle *h, int on);
  * start).  The network output is m (c + p), c the last convolution: a
  * learned correction of the linear extrapolation, zero where nothing moved.
  * Output unit: norm[6] metres of bed change.  Device tensors: X bf16
- * [B][T][T][8], targets/outputs float [B][T][T].  Training: MSE loss, Adam
- * (lr given, betas 0.9/0.999). */
+ * [B][T][T][8], targets/outputs float [B][T][T].  Training: MSE or L1
+ * loss, Adam (lr given, betas 0.9/0.999). */
 typedef struct swe_surrogate swe_surrogate;
 typedef struct {
     int64_t windows, surrogate_windows, plain_windows, judged, takeover_window;
@@ -281,10 +281,13 @@ swe_status swe_surrogate_create(int tile, int max_batch, uint64_t seed, void *cu
 swe_status swe_surrogate_destroy(swe_surrogate *s);
 /* The 8 normalisation constants above; norm[1], norm[3..7] must be > 0. */
 swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[8]);
+/* Training loss of swe_surrogate_train_step: 0 mean squared error (the
+ * default), 1 mean absolute error (the judged error is a relative L1). */
+swe_status swe_surrogate_set_loss(swe_surrogate *s, int kind);
 /* Forward pass of B tiles (X device bf16, out device float). */
 swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B);
-/* One training step on B tiles (forward, MSE loss, backward, Adam);
- * *loss_out (host) gets the mean squared error before the update. */
+/* One training step on B tiles (forward, loss, backward, Adam);
+ * *loss_out (host) gets the mean loss before the update. */
 swe_status swe_surrogate_train_step(swe_surrogate *s, const void *X, const float *target, int B, float lr,
                                     float *loss_out);
 /* Layer (0..5) parameters, FP32 host array W[nout][9*cin] then bias[nout]

@@ -4,7 +4,7 @@ A plain numpy restatement of the 6-layer 3x3 convolutional network that the
 tensor-core kernels run: conv3x3 with zero padding 1 written as im2col + a
 matrix product, ReLU on hidden layers, a linear last convolution whose output
 corrects the input's linear extrapolation inside the input's activity mask,
-and the backward pass of the mean-squared-error loss by the chain rule.  Only tests may import this
+and the backward pass of the mean squared or absolute error loss by the chain rule.  Only tests may import this
 module; it shares no code with the CUDA library.
 
 Layout: images [H][W][C]; weights W[nout][9*cin] with k = tap*cin + c and
@@ -52,17 +52,23 @@ def forward(X, params, round_fn=None):
     return acts, out
 
 
-def loss_and_grads(X, target, params, round_fn=None):
-    """Mean squared error over pixels and the gradients (dW, db) of every
-    layer by back-propagation; dgrad of conv3x3 is the correlation of the
-    output gradient with the spatially flipped, transposed kernel, here via
-    im2col of the output gradient."""
+def loss_and_grads(X, target, params, round_fn=None, loss="mse"):
+    """Mean squared (loss="mse") or absolute ("l1", subgradient 0 at a zero
+    residual) error over pixels and the gradients (dW, db) of every layer by
+    back-propagation; dgrad of conv3x3 is the correlation of the output
+    gradient with the spatially flipped, transposed kernel, here via im2col
+    of the output gradient."""
     r = round_fn or (lambda a: a)
     acts, out = forward(X, params, round_fn)
     H, W = out.shape
     d = out - target
-    loss = float(np.mean(d * d))
-    g = r((2.0 / (H * W)) * d * acts[0][:, :, 7])[:, :, None]   # dL/dz through out = m (z + p)
+    if loss == "l1":
+        value = float(np.mean(np.abs(d)))
+        dl = np.sign(d) / (H * W)
+    else:
+        value = float(np.mean(d * d))
+        dl = (2.0 / (H * W)) * d
+    g = r(dl * acts[0][:, :, 7])[:, :, None]             # dL/dz through out = m (z + p)
     grads = [None] * 6
     for i in range(5, -1, -1):
         Wm, b = params[i]
@@ -79,7 +85,7 @@ def loss_and_grads(X, target, params, round_fn=None):
         Wd = Wf.transpose(2, 1, 0).reshape(cin, -1)           # [cin][9*nout], k = tap*nout + n
         dX = (im2col(g) @ Wd.T).reshape(H, W, cin)
         g = r(dX * (xin > 0))                                 # through the ReLU of layer i-1
-    return loss, grads, out
+    return value, grads, out
 
 
 def random_params(seed, scale=1.0):

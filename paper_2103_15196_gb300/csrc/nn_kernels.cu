@@ -499,20 +499,23 @@ __global__ void adam_update(float *__restrict__ Wm, float *__restrict__ m, float
     }
 }
 
-// dOut = 2 m (out - target) / count as channel 0 of an NHWC8 BF16 tensor
-// (m: the activity mask, channel 7 of the input X; out = m (...));
-// the squared error is summed (per block) for the loss.
+// Loss gradient as channel 0 of an NHWC8 BF16 tensor, m the activity mask
+// (channel 7 of the input X; out = m (...)), d = out - target:
+//   l1 = 0: mean squared error, dOut = 2 m d / count;
+//   l1 = 1: mean absolute error, dOut = m sign(d) / count (0 at d = 0).
+// The per-pixel loss is summed (per block).
 __global__ void loss_grad(const float *__restrict__ out, const float *__restrict__ target,
-                          const __nv_bfloat16 *__restrict__ X, size_t count, __nv_bfloat16 *__restrict__ dOut,
+                          const __nv_bfloat16 *__restrict__ X, size_t count, int l1, __nv_bfloat16 *__restrict__ dOut,
                           float *__restrict__ loss_sum) {
     __shared__ float red[256];
     float s = 0.f;
-    const float scale = 2.f / (float)count;
+    const float scale = (l1 ? 1.f : 2.f) / (float)count;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const float d = out[i] - target[i];
-        s += d * d;
+        const float gd = l1 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : d;
+        s += l1 ? fabsf(d) : d * d;
         __align__(16) __nv_bfloat16 o[8];
-        o[0] = __float2bfloat16(__bfloat162float(X[i * 8 + 7]) * scale * d);
+        o[0] = __float2bfloat16(__bfloat162float(X[i * 8 + 7]) * scale * gd);
 #pragma unroll
         for (int j = 1; j < 8; ++j) o[j] = __float2bfloat16(0.f);
         reinterpret_cast<uint4 *>(dOut)[i] = reinterpret_cast<uint4 *>(o)[0];
@@ -641,6 +644,7 @@ struct swe_surrogate {
     long adam_t = 0;
     std::vector<void *> allocs;
     uint8_t *act = nullptr;
+    int l1 = 0;   // training loss: 0 mean squared error, 1 mean absolute error
     float h_norm[8] = {0, 1, 0, 1, 1, 1, 1, 1};
 };
 
@@ -748,10 +752,11 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
         if (e == cudaSuccess) e = salloc(s, (void **)&l.Wf, (size_t)l.noutp * l.kp * 2);
         if (e == cudaSuccess && i > 0) e = salloc(s, (void **)&l.Wd, (size_t)l.cin * l.kpd * 2);
         if (e == cudaSuccess) e = salloc(s, (void **)&l.grad, (size_t)l.mt * 128 * l.noutp * 4);
-        // He initialisation for the hidden layers, a small output layer
+        // He initialisation for the hidden layers
         std::vector<float> w(nw);
         const int fan_in = 9 * l.cin;
-        const float sd = i == 5 ? 0.01f : std::sqrt(2.f / fan_in);
+        // zero output layer: the untrained network is the linear extrapolation itself
+        const float sd = i == 5 ? 0.f : std::sqrt(2.f / fan_in);
         for (int n = 0; n < l.nout; ++n)
             for (int k = 0; k < 9 * l.cin; ++k) {
                 const int c = k % l.cin;
@@ -797,6 +802,12 @@ extern "C" swe_status swe_surrogate_set_norm(swe_surrogate *s, const float norm[
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
+extern "C" swe_status swe_surrogate_set_loss(swe_surrogate *s, int kind) {
+    if (!s || (kind != 0 && kind != 1)) return SWE_EINVAL;
+    s->l1 = kind;
+    return SWE_OK;
+}
+
 extern "C" swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B) {
     if (!s || !X || !out || B < 1 || B > s->maxB) return SWE_EINVAL;
     if (forward_all(s, (const __nv_bfloat16 *)X, out, B) != cudaSuccess) return SWE_ECUDA;
@@ -811,7 +822,7 @@ extern "C" swe_status swe_surrogate_train_step(swe_surrogate *s, const void *Xv,
     cudaError_t e = forward_all(s, X, s->out, B);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, 4, s->stream);
     if (e == cudaSuccess) {
-        loss_grad<<<grid_n(pix), 256, 0, s->stream>>>(s->out, target, X, pix, s->dOut, s->loss);
+        loss_grad<<<grid_n(pix), 256, 0, s->stream>>>(s->out, target, X, pix, s->l1, s->dOut, s->loss);
         e = cudaGetLastError();
     }
     // backward: gradient w.r.t. the pre-activations of layers 5..1, then weights
@@ -967,6 +978,12 @@ swe_status after_solver(swe_surrogate *s, const Coupling &k) {
     return cudaStreamSynchronize(k.hs) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
+// Orders the solver's next work after the surrogate's work so far.
+swe_status before_solver(swe_surrogate *s, const Coupling &k) {
+    if (k.hs == s->stream) return cudaGetLastError() == cudaSuccess ? SWE_OK : SWE_ECUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
 void launch_save(swe_surrogate *s, const Coupling &k, float *dst) {
     bed_tiles<<<grid_n(k.total), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, dst, k.total);
 }
@@ -1046,12 +1063,11 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
         swe_status r;
         if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
         launch_save(s, k, s->bsave);
-        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SWE_ECUDA;
-        if ((r = swe_run_steps(h, 1)) != SWE_OK) return r;
+        if ((r = before_solver(s, k)) != SWE_OK || (r = swe_run_steps(h, 1)) != SWE_OK) return r;
         if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
         launch_pack(s, k, s->X0);
         if (forward_all(s, s->X0, s->out, B) != cudaSuccess) return SWE_ECUDA;
-        return check_err(s);
+        return before_solver(s, k);   // the forward's error flag is read once per window
     };
     for (int w = 0; w < nwindows && rc == SWE_OK; ++w) {
         double t0 = 0, t1 = 0;
@@ -1065,6 +1081,7 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             if ((rc = first_step_and_predict()) != SWE_OK) break;
             if ((rc = swe_run_steps(h, K - 1)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
             if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
+            if ((rc = check_err(s)) != SWE_OK) break;
             launch_save(s, k, s->tgt);
             cudaMemsetAsync(dsum, 0, 5 * sizeof(double), s->stream);
             judge_sums<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->out, last, s->X0, s->norm, k.c->nx,
@@ -1101,7 +1118,7 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             }
             if ((rc = swe_get_time(h, &t1)) != SWE_OK) break;
             if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
-            if ((rc = launch_apply(s, h, k)) != SWE_OK) break;
+            if ((rc = check_err(s)) != SWE_OK || (rc = launch_apply(s, h, k)) != SWE_OK) break;
             st->bed_time += (t1 - t0) * f;
             st->water_time += t1 - t0;
             ++st->surrogate_windows;

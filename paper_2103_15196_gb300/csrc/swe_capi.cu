@@ -56,7 +56,8 @@ struct swe_handle {
     int diag_blocks = 0;
     void *allocs[32] = {};
     int nalloc = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;    // the graph for the current coupling (one of gcache)
+    cudaGraphExec_t gcache[2] = {};     // by sediment_on
     int graph_steps = 0;
     std::string err;
 };
@@ -209,10 +210,18 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     return SWE_OK;
 }
 
+// Step graphs are captured per coupling mode (Exner on / off) and dropped
+// whenever anything they bake in (parameters, buffers, tiling) changes.
+static void drop_graphs(swe_handle *h) {
+    for (cudaGraphExec_t &g : h->gcache)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    h->graph = nullptr;
+}
+
 extern "C" swe_status swe_destroy(swe_handle *h) {
     if (!h) return SWE_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    drop_graphs(h);
     for (int i = 0; i < h->nalloc; ++i) cudaFree(h->allocs[i]);
     if (h->h_dev) cudaFreeHost(h->h_dev);
     if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -249,7 +258,7 @@ static swe_status upload_manning(swe_handle *h, const std::vector<double> &n, in
     CU(h, cudaMemcpy(pb, bb.data(), bb.size(), cudaMemcpyHostToDevice));
     h->b.gn2 = pa; h->b.ajn = pb;
     h->c.man_shift = shift; h->c.man_w = w;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     return SWE_OK;
 }
 
@@ -300,7 +309,7 @@ extern "C" swe_status swe_set_sources(swe_handle *h, const uint8_t *mask, const 
     h->b.src_x = (const int *)px; h->b.hyd_t = (const double *)pt; h->b.hyd_q = (const double *)pq;
     h->c.nk = nkk;
     h->c.nsrc = nkk ? (int)xs.size() : 0;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     h->state_set = false;  // census and dt depend on the sources: set the state again
     return SWE_OK;
 }
@@ -324,7 +333,7 @@ extern "C" swe_status swe_set_bed_source(swe_handle *h, const double *q) {
     } else {
         h->c.hgs = h->p.hgs_skip ? 1 : 0;
     }
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     return SWE_OK;
 }
 
@@ -431,6 +440,7 @@ static swe_status free_stepping(swe_handle *h) {
 }
 
 static swe_status ensure_graph(swe_handle *h) {
+    h->graph = h->gcache[h->c.sediment_on ? 1 : 0];
     if (h->graph) return SWE_OK;
     long long ncell = (long long)h->c.nx * h->c.ny;
     int m = ncell >= (1ll << 24) ? 8 : (ncell >= (1ll << 20) ? 32 : 128);
@@ -444,6 +454,7 @@ static swe_status ensure_graph(swe_handle *h) {
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->graph = nullptr; return fail(h, SWE_ECUDA, cudaGetErrorString(e)); }
+    h->gcache[h->c.sediment_on ? 1 : 0] = h->graph;
     h->graph_steps = m;
     return SWE_OK;
 }
@@ -527,7 +538,7 @@ extern "C" swe_status swe_set_sediment(swe_handle *h, int on) {
     if (!h) return SWE_EINVAL;
     h->c.sediment_on = on ? 1 : 0;
     h->p.sediment_on = h->c.sediment_on;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    h->graph = nullptr;   // ensure_graph picks the cached graph of this coupling
     if (!h->state_set) return SWE_OK;
     // the Eq. 7 maxima depend on the coupling: gather them again for the current state
     CU(h, L_init(h));
@@ -627,7 +638,7 @@ int handle_retile(swe_handle *h, int bw, int th) {
     h->b.census[0] = (int *)cen0; h->b.census[1] = (int *)cen1; h->b.skipped = (unsigned char *)skp;
     h->bw = bw;
     c.tw = tw; c.th = th; c.tiles_x = tx; c.tiles_y = ty;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     if (!h->state_set) return SWE_OK;
     // census of the current state (its buffer is buf[n & 1]); the maxima the
     // census kernel gathers are those of the same state, so dt is unchanged

@@ -413,6 +413,10 @@ class Surrogate:
         a = (ctypes.c_float * 8)(*[float(x) for x in norm])
         self._check(self._L.swe_surrogate_set_norm(self._h, a))
 
+    def set_loss(self, kind):
+        """'mse' (default) or 'l1'."""
+        self._check(self._L.swe_surrogate_set_loss(self._h, {"mse": 0, "l1": 1}[kind]))
+
     def forward(self, X, out, B):
         self._check(self._L.swe_surrogate_forward(self._h, self._p(X), self._p(out), int(B)))
 

@@ -1,11 +1,11 @@
-"""Writes tests/golden/cfg2_oracle.npz: the FP64 CPU oracle's state after
+"""Writes tests/golden/flood2048_oracle.npz: the FP64 CPU oracle's state after
 10^4 steps of the 2048^2 flood-channel workload (fractal DEM seed 2, 40 m
 channel, 500 m^3/s triangular hydrograph, Manning n per 64x64 block, psi 0.4,
 K 0.4).  Calls only the oracle and the seeded input generators.
 
 Stored: final H, the bed change b - b0, t and the step count, plus input
 checksums so a consumer can verify it regenerated the same inputs.
-Usage: python tests/golden/make_cfg2_reference.py [nsteps]
+Usage: python tests/golden/make_flood2048_reference.py [nsteps]
 """
 import os
 import sys
@@ -28,7 +28,7 @@ def main(nsteps=10000):
     st = O.State(sc.H, sc.Hu, sc.Hv, sc.b)
     t0 = time.time()
     st, t, infos = O.run(p, st, n, nsteps, src=sc.src, hydro=O.Hydrograph(sc.hydro_t, sc.hydro_Q))
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cfg2_oracle.npz")
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "flood2048_oracle.npz")
     np.savez_compressed(out, H=st.H, db=st.b - sc.b, Hu=st.Hu, Hv=st.Hv, t=t, steps=len(infos),
                         b0_sum=float(sc.b.sum()), n_sum=float(sc.manning.sum()),
                         inflow=float(sum(i.inflow_vol for i in infos)))

@@ -43,13 +43,16 @@ def test_zero_last_layer_gives_masked_linear_extrapolation():
     assert not out.any() and all(not g.any() and not b.any() for g, b in grads)
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("loss", ["mse", "l1"])
+def test_gradients_match_finite_differences(loss):
     rng = np.random.default_rng(1)
     H = W = 6
     X = _features(rng, H, W)
     target = rng.normal(size=(H, W))
     params = C.random_params(2)
-    loss, grads, _ = C.loss_and_grads(X, target, params)
+    value, grads, out = C.loss_and_grads(X, target, params, loss=loss)
+    if loss == "l1":   # differentiable at these parameters: no residual near 0
+        assert np.abs(out - target).min() > 1e-3
     eps = 1e-6
     for layer in range(6):
         Wm, b = params[layer]
@@ -58,17 +61,17 @@ def test_gradients_match_finite_differences():
             k = rng.integers(Wm.shape[1])
             old = Wm[n, k]
             Wm[n, k] = old + eps
-            lp = C.loss_and_grads(X, target, params)[0]
+            lp = C.loss_and_grads(X, target, params, loss=loss)[0]
             Wm[n, k] = old - eps
-            lm = C.loss_and_grads(X, target, params)[0]
+            lm = C.loss_and_grads(X, target, params, loss=loss)[0]
             Wm[n, k] = old
             fd = (lp - lm) / (2 * eps)
             assert grads[layer][0][n, k] == pytest.approx(fd, rel=1e-5, abs=1e-9), (layer, n, k)
         n = rng.integers(b.shape[0])
         old = b[n]
         b[n] = old + eps
-        lp = C.loss_and_grads(X, target, params)[0]
+        lp = C.loss_and_grads(X, target, params, loss=loss)[0]
         b[n] = old - eps
-        lm = C.loss_and_grads(X, target, params)[0]
+        lm = C.loss_and_grads(X, target, params, loss=loss)[0]
         b[n] = old
         assert grads[layer][1][n] == pytest.approx((lp - lm) / (2 * eps), rel=1e-5, abs=1e-9), layer

@@ -81,17 +81,19 @@ def test_surrogate_forward_matches_cpu_reference(lib):
     S.close()
 
 
-def test_surrogate_gradients_match_cpu_reference(lib):
+@pytest.mark.parametrize("kind", ["mse", "l1"])
+def test_surrogate_gradients_match_cpu_reference(lib, kind):
     import torch
     from oracle import cnn_oracle as C
     T = 128
     S, used, Xb, Xd = _setup(4, T)
+    S.set_loss(kind)
     rng = np.random.default_rng(40)
     target = rng.normal(size=(T, T)).astype(np.float32)
     td = torch.from_numpy(target).cuda()[None].contiguous()
     loss = S.train_step(Xd, td, 1, 1e-30)
     torch.cuda.synchronize()
-    ref_loss, ref_grads, _ = C.loss_and_grads(Xb, target.astype(np.float64), used, round_fn=_bf16_round)
+    ref_loss, ref_grads, _ = C.loss_and_grads(Xb, target.astype(np.float64), used, round_fn=_bf16_round, loss=kind)
     assert loss == pytest.approx(ref_loss, rel=2e-2)
     for layer in range(6):
         gW, gb = S.grads(layer)

@@ -82,7 +82,7 @@ def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_censu
 
 
 def test_fp64_parity_dam_break_128(gpu, orc):
-    """Config 1: 128^2 dam break over the noisy erodible bed, 500 steps."""
+    """The 128^2 dam break over the noisy erodible bed, 500 steps."""
     sc = I.dam_break(128, 128, seed=1)
     worst = _per_step_parity(gpu, orc, sc, 500, bw=128, th=32)
     print("fp64 dam break worst rel Linf (H, Hu, Hv, b):", worst)
@@ -155,10 +155,10 @@ def test_hgs_skip_is_bit_exact_on_gpu(gpu, precision):
 
 
 def test_fp32_flood_channel_2048_full_run(gpu):
-    """Config 2: 2048^2 FP32 state vs the FP64 oracle after 10^4 steps, at the
+    """The 2048^2 flood channel: FP32 state vs the FP64 oracle after 10^4 steps, at the
     oracle's final time: relative L1 <= 1e-4 on H and b.  The oracle's final
-    state is stored by tests/golden/make_cfg2_reference.py (oracle only)."""
-    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "cfg2_oracle.npz"))
+    state is stored by tests/golden/make_flood2048_reference.py (oracle only)."""
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "flood2048_oracle.npz"))
     sc = I.flood_channel(2048, dx=5.0, seed=2, peak=500.0)
     assert sc.b.sum() == pytest.approx(float(ref["b0_sum"]), rel=1e-12)
     assert sc.manning.sum() == pytest.approx(float(ref["n_sum"]), rel=1e-12)
@@ -176,7 +176,7 @@ def test_fp32_flood_channel_2048_full_run(gpu):
     relb = np.abs(g[3] - b_ref).sum() / np.abs(b_ref).sum()
     db_o = ref["db"]
     rel_db = np.abs((g[3] - sc.b) - db_o).sum() / max(np.abs(db_o).sum(), 1e-30)
-    print(f"cfg2: steps gpu {n_gpu} oracle {int(ref['steps'])} t={t_ref:.3f} relL1 H {relH:.3e} "
+    print(f"flood 2048^2: steps gpu {n_gpu} oracle {int(ref['steps'])} t={t_ref:.3f} relL1 H {relH:.3e} "
           f"b {relb:.3e} bed-change {rel_db:.3e} wet {(H_ref > 1e-4).sum()} "
           f"vol gpu {d['water_volume']:.6e} oracle {H_ref.sum() * 25.0:.6e} inflow gpu {d['inflow_volume']:.6e} "
           f"oracle {float(ref['inflow']):.6e}")
