@@ -295,7 +295,8 @@ swe_status swe_surrogate_train_step(swe_surrogate *s, const void *X, const float
 swe_status swe_surrogate_params(swe_surrogate *s, int layer, float *host, int dir);
 /* Gradients of the last training step, same layout as swe_surrogate_params. */
 swe_status swe_surrogate_grads(swe_surrogate *s, int layer, float *host);
-/* Device pointer of an internal buffer: 0..4 layer outputs (bf16 NHWC32), 5 the network output. */
+/* Device pointer of an internal buffer: 0..4 layer outputs (bf16, 32 channels,
+ * row-planar [B][T][4][T][8]), 5 the network output. */
 swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **ptr);
 /* save_bed remembers the FP32 handle's current bed (the window's start);
  * pack_state writes the handle's current state as input tiles (device X,

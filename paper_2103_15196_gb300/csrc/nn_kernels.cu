@@ -109,80 +109,114 @@ extern "C" swe_status swe_nn_tc_selftest(int n, int k, const uint16_t *A, const 
 
 // ======================================================================
 // 3x3 convolutions (stride 1, zero padding 1) of the bed surrogate as
-// implicit GEMMs on the tensor cores.  Activations are NHWC BF16 with 8
-// (input) or 32 channels; weights are K-major BF16 [nout][k], k = tap * cin +
-// c, tap = (dy + 1) * 3 + (dx + 1).  One CTA of 128 threads computes 128
-// consecutive pixels of one image row x nout channels; the FP32 accumulator
-// lives in tensor memory (128 lanes x nout columns).
+// implicit GEMMs on the tensor cores.  Activations are BF16 with 8 (input)
+// or 32 channels in the row-planar layout below; weights are K-major BF16
+// [nout][k], k = tap * cin + c, tap = (dy + 1) * 3 + (dx + 1).  FP32
+// accumulators live in tensor memory (128 pixel lanes x nout columns).
 // ======================================================================
 
 namespace swe_nn {
 
 enum { EPI_RELU = 0, EPI_OUT = 1, EPI_MASK = 2 };
 
+// Activations are stored row-planar: [image][y][channel block][x][8]
+// (BF16), so that one row of one 8-channel block is contiguous.  With 8
+// channels this is plain NHWC.  Element offset of channel block cb of pixel
+// (x, y) of image img, for C channels:
+__device__ __forceinline__ size_t act_off(int img, int y, int x, int cb, int C, int H, int W) {
+    return ((((size_t)img * H + y) * (C / 8) + cb) * W + x) * 8;
+}
+
 template <int CIN> struct ConvK {
     static constexpr int K = 9 * CIN;
     static constexpr int KP = (K + 15) / 16 * 16;   // padded to whole MMAs
 };
 
-// cp.async of 16 bytes into shared memory; src_bytes = 0 writes zeros.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// 3x3 convolution with zero padding on the tensor cores, no im2col.  Epilogues:
-// EPI_RELU (forward, hidden layer): bias + ReLU -> NHWC32 BF16; EPI_OUT (the
-// output layer): m (channel 0 + bias + p) -> FP32 per pixel, where p and m
-// are channels 6 (the linear extrapolation of the bed change) and 7 (the
-// activity mask) of the network input, passed as `mask`; EPI_MASK (input
-// gradient): times (mask > 0) -> NHWC32 BF16.
+// 3x3 convolution with zero padding on the tensor cores (tcgen05, BF16 x
+// BF16 -> FP32 in tensor memory), no im2col.  Epilogues: EPI_RELU (forward,
+// hidden layer): bias + ReLU -> BF16; EPI_OUT (the output layer): m (channel
+// 0 + bias + p) -> FP32 per pixel, where p and m are channels 6 (the linear
+// extrapolation of the bed change) and 7 (the activity mask) of the network
+// input, passed as `mask`; EPI_MASK (input gradient): times (mask > 0) ->
+// BF16.
 //
-// Row streaming:
 // A CTA owns one 128-pixel column band of an image and a run of output rows.
-// Each input row it needs is loaded once, into a shared-memory slot of 136
-// pixels (x0-1 .. x0+134) in the K-major layout, the 136 rows of each 8-channel
-// column block contiguous (16 bytes per pixel, blocks CBS bytes apart).  The
-// A operand of tap (dy, dx) is then that slot read from pixel dx+1 on: the
-// same layout with the descriptor's start moved by 16 (dx+1) bytes.  With 32
-// channels a tap is two MMAs (K = 16 channels each, LBO = CBS); with 8
-// channels one MMA covers the taps (dy, dx) and (dy, dx+1), LBO = 16 bytes
-// (one pixel), and the weights carry a zero block for the unused pair
-// partner.  Five row slots and two TMEM accumulator halves pipeline the rows:
-// while the MMAs of row y run, the CTA stores row y-1, and rows y+2 and y+3
-// stream in with cp.async.
-template <int CIN> struct RowConv {
-    static constexpr int KR = CIN == 8 ? 96 : 9 * CIN;   // K of the MMA sequence
-    static constexpr int RP = 136;                        // pixels per row slot
-    static constexpr int CBS = RP * 16 + 16;              // column-block stride (padded against bank conflicts)
-    static constexpr int SLOT = (CIN / 8) * CBS;
-    static constexpr int NS = 5;                          // row slots
-    template <int NOUT> static constexpr size_t smem() { return (size_t)NOUT * KR * 2 + (size_t)NS * SLOT + 64; }
+// Each input row is loaded once, by bulk copies of its contiguous row
+// segments (one per 8-channel block, pixels x0-1 .. x0+134 clipped to the
+// image), into a slot laid out K-major: the 136 pixels of a channel block
+// 16 bytes apart, blocks CBS bytes apart.  The A operand of tap (dy, dx) is
+// that slot read from pixel dx+1 on: the same layout with the descriptor's
+// start moved by 16 (dx+1) bytes.  With 32 channels a tap is two MMAs (K = 16
+// channels each, LBO = CBS); with 8 channels one MMA covers the taps (dy, dx)
+// and (dy, dx+1), LBO = 16 bytes (one pixel), and the weights carry a zero
+// block for the unused pair partner.  Pixels outside the image stay at the
+// zeros written when the CTA starts; rows outside the image are not loaded and
+// their taps are not issued.  Warp roles, with no block-wide barrier in the
+// row loop:
+//   warp 4, lane 0  - producer: bulk copies of input rows into a ring of NS
+//                     slots (mbarrier `full` per slot), each slot refilled
+//                     once `freed`;
+//   warp 5, lane 0  - MMA issuer: R output rows at a time, their MMAs
+//                     interleaved so that R accumulation chains (TMEM stages)
+//                     are in flight together; tcgen05.commit to `accf` (stage
+//                     ready) and `freed` (the slot of a row no longer needed);
+//   warps 0-3       - epilogue: wait `accf`, read the stage from TMEM, release
+//                     it (`acce`), then convert and store.
+// Output row j (y = ya + j) reads input rows q = j, j+1, j+2 (y-1, y, y+1);
+// input row q is freed by the commit after output row q's MMAs.  All waits
+// are bounded; a timeout raises a shared abort flag that ends every role's
+// waits, the producer and the MMA issuer then let their copies and MMAs in
+// flight finish, and *err is set.
+template <int CIN, int R> struct WsConv {
+    static constexpr int KR = CIN == 8 ? 96 : 9 * CIN;
+    static constexpr int CB = CIN / 8;
+    static constexpr int CBS = 136 * 16;                  // 2176 B: a 128-byte multiple (TMA destination)
+    static constexpr int SLOT = CB * CBS;
+    static constexpr int NACC = 2 * R;                    // TMEM stages of 32 columns
+    static constexpr int NS = 2 * R + 2;                  // input row slots
+    static constexpr int TCOLS = NACC * 32;
+    template <int NOUT> static constexpr size_t smem() {
+        return (size_t)NOUT * KR * 2 + (size_t)NS * SLOT + (2 * NS + 2 * NACC) * 8 + 16;
+    }
 };
 
-template <int CIN, int NOUT, int EPI>
-__global__ void __launch_bounds__(128)
-conv3x3_row(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
-            const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf, int H,
-            int W, int rows, int *err) {
-    using RC = RowConv<CIN>;
+// Bounded wait on an mbarrier phase: try_wait (which suspends briefly in
+// hardware) without sleeping for the first polls, then with a short back-off.
+__device__ __forceinline__ bool ws_wait(uint64_t *mbar, uint32_t parity, volatile int *abort, bool honour_abort) {
+    for (int i = 0; i < kPolls; ++i) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (honour_abort && *abort) return false;
+        if (i > 256) __nanosleep(64);
+    }
+    *abort = 1;
+    return false;
+}
+
+template <int CIN, int NOUT, int EPI, int R>
+__global__ void __launch_bounds__(192)
+conv3x3_ws(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt,
+           const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y,
+           float *__restrict__ Yf, int H, int W, int rows, int *err) {
+    using WC = WsConv<CIN, R>;
     constexpr int KPS = ConvK<CIN>::KP;
-    constexpr int KR = RC::KR, NMMA = KR / 16, CB = CIN / 8, CBS = RC::CBS, SLOT = RC::SLOT, NS = RC::NS;
+    constexpr int KR = WC::KR, NMMA = KR / 16, CB = WC::CB, CBS = WC::CBS, SLOT = WC::SLOT;
+    constexpr int NS = WC::NS, NACC = WC::NACC;
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sb = sm;                       // NOUT x KR
-    unsigned char *slots = sm + NOUT * KR * 2;    // NS x SLOT
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(slots + NS * SLOT);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    unsigned char *sb = sm;                                   // NOUT x KR weights
+    unsigned char *slots = sm + NOUT * KR * 2;                // NS x SLOT
+    uint64_t *full = reinterpret_cast<uint64_t *>(slots + NS * SLOT);
+    uint64_t *freed = full + NS;
+    uint64_t *accf = freed + NS;
+    uint64_t *acce = accf + NACC;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + NACC);
+    volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int x0 = blockIdx.x * 128, ya = blockIdx.y * rows, img = blockIdx.z;
-    const int yb = min(ya + rows, H);
+    const int nrows = min(ya + rows, H) - ya;                 // >= 1
+    const int nin = nrows + 2;
     const size_t plane = (size_t)H * W;
-    const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
 
-    // weights, in the order of the MMA sequence
-    for (int i = t; i < NOUT * (KR / 8); i += 128) {
+    for (int i = t; i < NOUT * (KR / 8); i += blockDim.x) {
         const int r = i / (KR / 8), kb = i % (KR / 8);
         uint4 v = make_uint4(0, 0, 0, 0);
         if (CIN == 8) {
@@ -193,124 +227,143 @@ conv3x3_row(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict
         }
         *reinterpret_cast<uint4 *>(sb + kmajor_off(r, kb * 8, NOUT)) = v;
     }
-
-    // slot of input row yy (yy >= -1)
-    auto slot_of = [&](int yy) { return slots + ((yy + NS) % NS) * SLOT; };
-    // one cp.async group per call (empty when the row is not needed)
-    auto load_row = [&](int yy, bool need) {
-        if (need) {
-            unsigned char *slot = slot_of(yy);
-            const bool rin = yy >= 0 && yy < H;
-            for (int i = t; i < RC::RP * CB; i += 128) {
-                const int j = i / CB, cb = i % CB;
-                const int xx = x0 - 1 + j;
-                const bool in = rin && xx >= 0 && xx < W;
-                const __nv_bfloat16 *src = in ? Xi + ((size_t)yy * W + xx) * CIN + cb * 8 : X;
-                cp_async16(slot + cb * CBS + j * 16, src, in ? 16 : 0);
-            }
-        }
-        cp_async_commit();
-    };
-
-    auto epilogue = [&](int y, uint32_t taddr) {
-        float v[32];
-        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
-        const int p = warp * 32 + lane, xx = x0 + p;
-        if (xx >= W) return;
-        const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
-        if (EPI == EPI_OUT) {
-            const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * 8 + 6);
-            Yf[pix] = __high2float(pm) * (v[0] + bias[0] + __low2float(pm));
-        } else {
-            __align__(16) __nv_bfloat16 o[32];
-            if (EPI == EPI_RELU) {
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(fmaxf(v[jj] + bias[jj], 0.f));
-            } else {
-                __align__(16) __nv_bfloat16 m[32];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(m)[q] = reinterpret_cast<const uint4 *>(mask + pix * 32)[q];
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(__bfloat162float(m[jj]) > 0.f ? v[jj] : 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(Y + pix * 32)[q] = reinterpret_cast<uint4 *>(o)[q];
-        }
-    };
-
-    if (warp == 0) tmem_alloc(tslot, 64);
-    if (t == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
-    load_row(ya - 1, true);
-    load_row(ya, true);
-    load_row(ya + 1, true);
-    load_row(ya + 2, ya + 2 <= yb);
+    // zero the slots: pixels outside the image are never written again
+    for (int i = t; i < NS * SLOT / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(slots)[i] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+    if (warp == 0) tmem_alloc(tslot, WC::TCOLS);
+    if (t == 0) {
+        for (int q = 0; q < NS; ++q) { mbar_init(&full[q], 1); mbar_init(&freed[q], 1); }
+        for (int a = 0; a < NACC; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 4); }
+        *abort = 0;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t phases = 0;   // bit h: parity of the next phase of mbar[h]
-    bool ok = true;
-    int it = 0;
-    for (int y = ya; y < yb && ok; ++y, ++it) {
-        const int half = it & 1;
-        // rows y-1 .. y+1 have landed (only the group of row y+2 may be pending)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (t == 0) {
-#pragma unroll 1
-            for (int m = 0; m < NMMA; ++m) {
-                uint32_t astart, lbo;
-                if (CIN == 8) {
-                    const int dyi = m / 2, pair = m % 2;
-                    astart = smem_u32(slot_of(y + dyi - 1)) + pair * 2 * 16;
-                    lbo = 16;
-                } else {
-                    const int tap = m / 2, hc = m % 2, dyi = tap / 3, dxi = tap % 3;
-                    astart = smem_u32(slot_of(y + dyi - 1)) + hc * 2 * CBS + dxi * 16;
-                    lbo = CBS;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            const int xs = max(x0 - 1, 0), xe = min(x0 + 135, W);   // pixels [xs, xe) of the row segment
+            const uint32_t seg = (uint32_t)(xe - xs) * 16;
+            int q = 0;
+            bool ok = true;
+            for (; q < nin; ++q) {
+                const int sl = q % NS, yy = ya - 1 + q;
+                if (q >= NS && !(ok = ws_wait(&freed[sl], (uint32_t)((q / NS) - 1) & 1u, abort, true))) break;
+                if (yy < 0 || yy >= H) {      // not loaded: its taps are skipped
+                    mbar_arrive(&full[sl]);
+                    continue;
                 }
-                const uint64_t ad = smem_desc(astart, lbo, 128);
-                const uint64_t bd = smem_desc(smem_u32(sb) + m * NOUT * 32, NOUT * 16, 128);
-                mma_bf16(tmem + half * 32, ad, bd, idesc_bf16_f32(NOUT), m > 0 ? 1u : 0u);
+                mbar_arrive_expect_tx(&full[sl], CB * seg);
+#pragma unroll
+                for (int cb = 0; cb < CB; ++cb)
+                    bulk_load(slots + sl * SLOT + cb * CBS + (xs - (x0 - 1)) * 16, X + act_off(img, yy, xs, cb, CIN, H, W),
+                              seg, &full[sl]);
             }
-            mma_commit(&mbar[half]);
+            if (!ok) atomicOr(err, 1);
+            // the copies of the last rows issued must land before the CTA ends
+            for (int p = max(0, q - NS); p < q; ++p) ws_wait(&full[p % NS], (uint32_t)(p / NS) & 1u, abort, false);
         }
-        if (it > 0) {
-            const int pb = half ^ 1;
-            ok = __syncthreads_and(mbar_wait(&mbar[pb], (phases >> pb) & 1u, kPolls));
-            phases ^= 1u << pb;
+    } else if (warp == 5) {
+        if (lane == 0) {
+            int landed = 0, issued = 0;
+            bool ok = true;
+            for (int j0 = 0; j0 < nrows && ok; j0 += R) {
+                const int nb = min(R, nrows - j0);
+                while (ok && landed < j0 + nb + 2) {
+                    ok = ws_wait(&full[landed % NS], (uint32_t)(landed / NS) & 1u, abort, true);
+                    if (ok) ++landed;
+                }
+                for (int r = 0; r < nb && ok; ++r) {
+                    const int j = j0 + r;
+                    if (j >= NACC) ok = ws_wait(&acce[j % NACC], (uint32_t)((j / NACC) - 1) & 1u, abort, true);
+                }
+                if (!ok) break;
+                tc_fence_after();
+                unsigned started = 0;   // bit r: row j0 + r has its first MMA
+#pragma unroll 1
+                for (int m = 0; m < NMMA; ++m) {
+                    uint32_t aoff, lbo, dyi;
+                    if (CIN == 8) {
+                        dyi = m / 2;
+                        aoff = (m % 2) * 2 * 16;
+                        lbo = 16;
+                    } else {
+                        const int tap = m / 2;
+                        dyi = tap / 3;
+                        aoff = (m % 2) * 2 * CBS + (tap % 3) * 16;
+                        lbo = CBS;
+                    }
+                    const uint64_t bd = smem_desc(smem_u32(sb) + m * NOUT * 32, NOUT * 16, 128);
+                    for (int r = 0; r < nb; ++r) {
+                        const int j = j0 + r, y = ya + j;
+                        if ((dyi == 0 && y == 0) || (dyi == 2 && y == H - 1)) continue;   // row outside the image
+                        const uint64_t ad = smem_desc(smem_u32(slots + ((j + dyi) % NS) * SLOT) + aoff, lbo, 128);
+                        mma_bf16(tmem + (j % NACC) * 32, ad, bd, idesc_bf16_f32(NOUT), (started >> r) & 1u);
+                        started |= 1u << r;
+                    }
+                }
+                for (int r = 0; r < nb; ++r) {
+                    mma_commit(&accf[(j0 + r) % NACC]);
+                    mma_commit(&freed[(j0 + r) % NS]);
+                }
+                issued = j0 + nb;
+            }
+            if (!ok) atomicOr(err, 1);
+            // MMAs in flight must finish before the tensor memory is freed
+            if (issued > 0) {
+                const int jl = issued - 1;
+                ws_wait(&freed[jl % NS], (uint32_t)(jl / NS) & 1u, abort, false);
+            }
+        }
+    } else {
+        for (int j = 0; j < nrows; ++j) {
+            const int a = j % NACC;
+            if (!ws_wait(&accf[a], (uint32_t)(j / NACC) & 1u, abort, true)) {
+                if (lane == 0) atomicOr(err, 1);
+                break;
+            }
             tc_fence_after();
-            if (ok) epilogue(y - 1, tmem + pb * 32);
+            float v[32];
+            tmem_ld32(tmem + a * 32 + ((uint32_t)(warp * 32) << 16), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[a]);
+            const int p = warp * 32 + lane, xx = x0 + p, y = ya + j;
+            if (xx >= W) continue;
+            if (EPI == EPI_OUT) {
+                const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
+                const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * 8 + 6);
+                Yf[pix] = __high2float(pm) * (v[0] + bias[0] + __low2float(pm));
+            } else {
+                __align__(16) __nv_bfloat16 o[32];
+                if (EPI == EPI_RELU) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(fmaxf(v[jj] + bias[jj], 0.f));
+                } else {
+                    __align__(16) __nv_bfloat16 mk[32];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<uint4 *>(mk)[q] = *reinterpret_cast<const uint4 *>(mask + act_off(img, y, xx, q, 32, H, W));
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(__bfloat162float(mk[jj]) > 0.f ? v[jj] : 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(Y + act_off(img, y, xx, q, 32, H, W)) = reinterpret_cast<uint4 *>(o)[q];
+            }
         }
-        // the slot of row y+3 held row y-2, last read by the MMAs of row y-1
-        if (ok) load_row(y + 3, y + 3 <= yb);
     }
-    if (ok && it > 0) {
-        const int pb = (it - 1) & 1;
-        ok = __syncthreads_and(mbar_wait(&mbar[pb], (phases >> pb) & 1u, kPolls));
-        phases ^= 1u << pb;
-        tc_fence_after();
-        if (ok) epilogue(yb - 1, tmem + pb * 32);
-    }
-    if (!ok) {
-        // let MMAs in flight finish before the tensor memory is freed
-        if (t == 0) atomicOr(err, 1);
-        __syncthreads_and(mbar_wait(&mbar[0], phases & 1u, kPolls));
-        __syncthreads_and(mbar_wait(&mbar[1], (phases >> 1) & 1u, kPolls));
-    }
-    cp_async_wait_all();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 64);
+    if (warp == 0) tmem_dealloc(tmem, WC::TCOLS);
 }
 
 // Weight gradient: dW[k][n] = sum_p Xpatch[p][k] dY[p][n] (k = tap*CIN + c;
 // row 9*CIN is a row of ones, giving the bias gradient sum_p dY[p][n]).
 // GEMM D[k][n] = A[k][p] B[n][p]^T over 128-pixel chunks, A and B K-major
-// over pixels, built by transposing the NHWC loads in shared memory.  Each
+// over pixels, built by transposing the activation loads in shared memory.  Each
 // CTA sums `rows` image rows; partial[cta][MT*128][NOUT] is reduced later.
 // DYC: channels stored per pixel in dY (32, or 8 for the output layer).
 template <int CIN, int NOUT, int DYC>
@@ -325,9 +378,6 @@ wgrad_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ 
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int img = blockIdx.y, y0 = blockIdx.x * rows;
-    const size_t plane = (size_t)H * W;
-    const __nv_bfloat16 *Xi = X + (size_t)img * plane * CIN;
-    const __nv_bfloat16 *Di = dY + (size_t)img * plane * DYC;
     const __nv_bfloat16 one = __float2bfloat16(1.f), zero = __float2bfloat16(0.f);
 
     // zero the tiles once (padding rows stay zero); the ones row is rewritten below
@@ -364,7 +414,7 @@ wgrad_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ 
                 for (int cg = 0; cg < CIN / 8; ++cg) {
                     __align__(16) __nv_bfloat16 v[8];
                     if (in) reinterpret_cast<uint4 *>(v)[0] =
-                        *reinterpret_cast<const uint4 *>(Xi + ((size_t)sy * W + sx) * CIN + cg * 8);
+                        *reinterpret_cast<const uint4 *>(X + act_off(img, sy, sx, cg, CIN, H, W));
                     else reinterpret_cast<uint4 *>(v)[0] = make_uint4(0, 0, 0, 0);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -384,7 +434,7 @@ wgrad_tc(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ 
                 if (xp < W) {
 #pragma unroll
                     for (int q = 0; q < DYC / 8; ++q)
-                        reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(Di + ((size_t)yy * W + xp) * DYC)[q];
+                        reinterpret_cast<uint4 *>(v)[q] = *reinterpret_cast<const uint4 *>(dY + act_off(img, yy, xp, q, DYC, H, W));
                 } else {
 #pragma unroll
                     for (int q = 0; q < DYC / 8; ++q) reinterpret_cast<uint4 *>(v)[q] = make_uint4(0, 0, 0, 0);
@@ -658,16 +708,39 @@ cudaError_t salloc(swe_surrogate *s, void **p, size_t bytes) {
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
+constexpr int kConvR = 2;   // output rows whose MMA chains run together
+
 template <int CIN, int NOUT, int EPI>
 cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, const __nv_bfloat16 *Wt, const float *bias,
                  const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B) {
     (void)l;
-    // at least 30 KB of shared memory: at most 7 CTAs (448 TMEM columns) per SM
-    const size_t smem = std::max<size_t>(RowConv<CIN>::template smem<NOUT>(), 30 * 1024);
-    cudaFuncSetAttribute(conv3x3_row<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int rows = 16;
-    dim3 grid((s->T + 127) / 128, (s->T + rows - 1) / rows, B);
-    conv3x3_row<CIN, NOUT, EPI><<<grid, 128, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
+    using WC = WsConv<CIN, kConvR>;
+    auto kern = conv3x3_ws<CIN, NOUT, EPI, kConvR>;
+    // enough shared memory that the CTAs of one SM fit its 512 TMEM columns
+    static const size_t smem =
+        std::max<size_t>(WC::template smem<NOUT>(), (size_t)(227 * 1024) / (512 / WC::TCOLS) - 1024);
+    static int resident = 0;
+    if (resident == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess) return e;
+        // CTAs per SM: shared memory, tensor memory (512 columns), threads
+        const int per_sm = std::min({smem_sm / (int)(smem + reserved), 512 / WC::TCOLS, 2048 / 192});
+        resident = std::max(1, per_sm) * sms;
+    }
+    // one wave: the column bands x images share the resident CTAs, each CTA
+    // streams a run of rows (at least 8, to amortise its set-up)
+    const int bands = (s->T + 127) / 128;
+    const int groups = std::max(1, resident / (bands * B));
+    const int rows = std::max(8, (s->T + groups - 1) / groups);
+    dim3 grid(bands, (s->T + rows - 1) / rows, B);
+    kern<<<grid, 192, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
     return cudaGetLastError();
 }
 
@@ -889,7 +962,7 @@ extern "C" swe_status swe_surrogate_grads(swe_surrogate *s, int layer, float *ho
 }
 
 // Internal activation buffers (device pointers) for tests: index 0..4 = the
-// outputs of layers 1..5 (NHWC32 BF16), 5 = the output (FP32 per pixel).
+// outputs of layers 1..5 (32-channel BF16, row-planar), 5 = the output (FP32 per pixel).
 extern "C" swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **ptr) {
     if (!s || !ptr || index < 0 || index > 5) return SWE_EINVAL;
     *ptr = index < 5 ? (void *)s->A[index] : (void *)s->out;

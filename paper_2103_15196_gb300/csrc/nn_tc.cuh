@@ -99,6 +99,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int m
     return false;
 }
 
+// One arrival on an mbarrier (a thread's part of its expected count).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous (TMA) writes the
+// current phase must wait for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy (TMA, 1-D): `bytes` contiguous bytes from global to shared
+// memory, completing on *mbar.  Both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // 32 consecutive FP32 accumulator columns of this thread's TMEM lane
 // (warp w reads lanes 32w..32w+31; taddr must carry lane base 32w << 16).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
