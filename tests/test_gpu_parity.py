@@ -54,8 +54,10 @@ def _fp64_solver(gpu, sc, bw=128, th=32, **kw):
     return S
 
 
-def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, **kw):
+def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, qb=None, **kw):
     S = _fp64_solver(gpu, sc, bw=bw, th=th, **kw)
+    if qb is not None:
+        S.set_bed_source(qb)
     d = S.diag()
     p = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, tile_x=d["tile_x"], tile_y=d["tile_y"], **kw)
     n_cell = sc.manning_per_cell()
@@ -64,7 +66,7 @@ def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_censu
     t = 0.0
     worst = np.zeros(4)
     for it in range(nsteps):
-        o, info = orc.step(p, st, n_cell, src=sc.src, hydro=hydro, t=t)
+        o, info = orc.step(p, st, n_cell, src=sc.src, qb=qb, hydro=hydro, t=t)
         dt = S.step()
         g = S.get_state()
         assert dt == pytest.approx(info.dt, rel=1e-13, abs=0), it
@@ -116,6 +118,72 @@ def test_fp64_parity_tiny_and_thin_grids(gpu, orc, shape):
     b = g.uniform(-0.05, 0.05, (ny, nx))
     sc = I.Scenario(nx, ny, 1.0, H, Hu, Hv, b, np.full((1, 1), 0.03), manning_block=256)
     _per_step_parity(gpu, orc, sc, 20, bw=128, th=32, A_J=0.05)
+
+
+def _moving_sediment_case(side=96, seed=41):
+    """Half-wet terrain with a 2 m dam-break step and an inflow hydrograph,
+    per-cell Manning n."""
+    sc = I.ensemble_scenario(side, seed=seed, manning=0.03, peak=200.0, d50_scale=1.0)
+    sc = I.Scenario(side, side, sc.dx, sc.H, sc.Hu, sc.Hv, sc.b, np.full((side, side), 0.03),
+                    manning_block=1, src=sc.src, hydro_t=sc.hydro_t, hydro_Q=sc.hydro_Q)
+    return sc
+
+
+@pytest.mark.parametrize("opts", [
+    {"sediment_on": 0},
+    {"aj_mode": 1},
+    {"dt_literal_D": 1, "A_J": 0.05},
+    {"hgs_skip": 0, "A_J": 0.02},
+    {"bed_source": True},
+], ids=["exner_off", "aj_from_eq4", "literal_D", "hgs_off", "bed_source"])
+def test_fp64_parity_options(gpu, orc, opts):
+    """The step's options against the oracle, per step: the Exner coupling
+    off (the surrogate's water-only steps), A_J from Eq. 4, the printed Eq. 7
+    D term, HGS skipping off, and a bed source field, with per-cell Manning
+    and an inflow hydrograph on partially wet terrain."""
+    sc = _moving_sediment_case()
+    kw = {k: v for k, v in opts.items() if k != "bed_source"}
+    qb = None
+    if opts.get("bed_source"):
+        g = I.rng(43)
+        qb = g.normal(0.0, 1e-4, (sc.ny, sc.nx))
+    p0 = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, **kw)
+    st, t, _ = orc.run(p0, orc.State(sc.H, sc.Hu, sc.Hv, sc.b), sc.manning_per_cell(), 40, src=sc.src,
+                       qb=qb, hydro=orc.Hydrograph(sc.hydro_t, sc.hydro_Q))
+    sc.H, sc.Hu, sc.Hv, sc.b = st.H, st.Hu, st.Hv, st.b
+    worst = _per_step_parity(gpu, orc, sc, 30, bw=128, th=16, qb=qb, **kw)
+    print("fp64 options", opts, "worst rel Linf:", worst)
+
+
+def test_fp32_ragged_multi_tile_per_step(gpu, orc):
+    """FP32 state, element by element against the FP64 oracle one step at a
+    time from the same inputs, on a 333 x 271 grid (2 x 9 blocks of 248 x 32
+    with ragged right and bottom edges): the per-step FP32 bound of the
+    full-size test (4e-5 m on H and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta)."""
+    nx, ny = 333, 271
+    side = max(nx, ny)
+    base = I.ensemble_scenario(side, seed=48, manning=0.035, peak=300.0, d50_scale=1.0)
+    H, Hu, Hv, b = (a[:ny, :nx].astype(np.float64) for a in (base.H, base.Hu, base.Hv, base.b))
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32)
+    S.set_manning(np.full((ny, nx), 0.035), block=0)
+    S.set_state(H, Hu, Hv, b)
+    p = orc.Params(nx=nx, ny=ny, dx=base.dx)
+    ncell = np.full((ny, nx), 0.035)
+    worst = np.zeros(4)
+    for it in range(25):
+        st = orc.State(*S.get_state(np.float32))
+        st = orc.State(*(a.astype(np.float64) for a in st.arrays()))
+        o, info = orc.step(p, st, ncell)
+        dt = S.step()
+        assert dt == pytest.approx(info.dt, rel=1e-5), it
+        got = S.get_state(np.float32)
+        for q in range(4):
+            e = np.abs(got[q].astype(np.float64) - o.arrays()[q])
+            tol = 4e-5 + (2e-5 * np.abs(o.arrays()[q]) if q in (1, 2) else 0.0)
+            worst[q] = max(worst[q], e.max())
+            assert np.all(e <= tol), (it, q, e.max())
+    S.close()
+    print("fp32 ragged per-step worst abs err (H, Hu, Hv, b):", worst)
 
 
 def test_fp64_advance_lands_on_t_end(gpu, orc):
