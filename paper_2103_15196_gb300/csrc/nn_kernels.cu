@@ -140,43 +140,53 @@ template <int CIN> struct ConvK {
 // input, passed as `mask`; EPI_MASK (input gradient): times (mask > 0) ->
 // BF16.
 //
-// A CTA owns one 128-pixel column band of an image and a run of output rows.
-// Each input row is loaded once, by bulk copies of its contiguous row
-// segments (one per 8-channel block, pixels x0-1 .. x0+134 clipped to the
-// image), into a slot laid out K-major: the 136 pixels of a channel block
-// 16 bytes apart, blocks CBS bytes apart.  The A operand of tap (dy, dx) is
-// that slot read from pixel dx+1 on: the same layout with the descriptor's
-// start moved by 16 (dx+1) bytes.  With 32 channels a tap is two MMAs (K = 16
-// channels each, LBO = CBS); with 8 channels one MMA covers the taps (dy, dx)
-// and (dy, dx+1), LBO = 16 bytes (one pixel), and the weights carry a zero
-// block for the unused pair partner.  Pixels outside the image stay at the
-// zeros written when the CTA starts; rows outside the image are not loaded and
-// their taps are not issued.  Warp roles, with no block-wide barrier in the
-// row loop:
+// A CTA owns one 128-pixel column band of an image and a run of output rows,
+// computed four at a time.  Each input row is loaded once, by bulk copies of
+// its contiguous row segments (one per 8-channel block, pixels x0-1 ..
+// x0+134 clipped to the image), into a slot laid out K-major: the 136 pixels
+// of a channel block 16 bytes apart, blocks CBS bytes apart.  The A operand
+// of column tap dx is that slot read from pixel dx+1 on (the descriptor's
+// start moved by 16 (dx+1) bytes); with 8 input channels one MMA covers two
+// neighbouring column taps (LBO = 16 bytes).
+//
+// An input row feeds at most three of the four output rows, through the
+// weights of row taps dy = +1, 0, -1 (in that order of output row).  The
+// weights of each K-slice (column tap and channel half) are stored as a
+// 3-block array [W(dy=+1); W(0); W(-1)] of NOUT rows each, so that one MMA per
+// input row and K-slice covers all the output rows it feeds: N = NOUT x
+// (rows fed), B = the matching sub-range of the array, D = the accumulator
+// columns of those rows (row r at column r NOUT).  A batch of four output
+// rows takes 6 x 6 + 1 MMAs (32 channels; 6 x 2 + 1 with 8) instead of 4 x 18:
+// the MMA cost is per instruction (about 151 cycles for any N <= 256), so
+// wider MMAs are faster.  The extra MMA zeroes the accumulator (zero A and B).
+// Pixels outside the image stay at the zeros written when the CTA starts;
+// rows outside it are not loaded and their MMAs are not issued.
+//
+// Warp roles, with no block-wide barrier in the row loop:
 //   warp 4, lane 0  - producer: bulk copies of input rows into a ring of NS
 //                     slots (mbarrier `full` per slot), each slot refilled
 //                     once `freed`;
-//   warp 5, lane 0  - MMA issuer: R output rows at a time, their MMAs
-//                     interleaved so that R accumulation chains (TMEM stages)
-//                     are in flight together; tcgen05.commit to `accf` (stage
-//                     ready) and `freed` (the slot of a row no longer needed);
-//   warps 0-3       - epilogue: wait `accf`, read the stage from TMEM, release
-//                     it (`acce`), then convert and store.
-// Output row j (y = ya + j) reads input rows q = j, j+1, j+2 (y-1, y, y+1);
-// input row q is freed by the commit after output row q's MMAs.  All waits
-// are bounded; a timeout raises a shared abort flag that ends every role's
-// waits, the producer and the MMA issuer then let their copies and MMAs in
-// flight finish, and *err is set.
-template <int CIN, int R> struct WsConv {
-    static constexpr int KR = CIN == 8 ? 96 : 9 * CIN;
+//   warp 5, lane 0  - MMA issuer: a batch of four output rows into one of two
+//                     TMEM stages; tcgen05.commit to `accf` (stage ready) and
+//                     `freed` (input rows no later batch needs);
+//   warps 0-3       - epilogue: wait `accf`, read the stage from TMEM row by
+//                     row, release it (`acce`), convert and store.
+// Output row j (y = ya + j) reads input rows q = j, j+1, j+2 (y-1, y, y+1).
+// All waits are bounded; a timeout raises a shared abort flag that ends every
+// role's waits, the producer and the MMA issuer then let their copies and MMAs
+// in flight finish, and *err is set.
+template <int CIN, int NOUT> struct WsConv {
     static constexpr int CB = CIN / 8;
-    static constexpr int CBS = 136 * 16;                  // 2176 B: a 128-byte multiple (TMA destination)
+    static constexpr int CBS = 136 * 16;                  // 2176 B: a 128-byte multiple (bulk-copy destination)
     static constexpr int SLOT = CB * CBS;
-    static constexpr int NACC = 2 * R;                    // TMEM stages of 32 columns
-    static constexpr int NS = 2 * R + 2;                  // input row slots
-    static constexpr int TCOLS = NACC * 32;
-    template <int NOUT> static constexpr size_t smem() {
-        return (size_t)NOUT * KR * 2 + (size_t)NS * SLOT + (2 * NS + 2 * NACC) * 8 + 16;
+    static constexpr int NSLICE = CIN == 8 ? 2 : 6;       // K-slices per input row
+    static constexpr int WSL = 3 * NOUT * 16 * 2;         // bytes of one K-slice's 3-block weight array
+    static constexpr int ZERO = 128 * 16 * 2;             // a zero 128 x 16 tile
+    static constexpr int NS = 10;                         // input row slots: a batch's 6 + the next 4
+    static constexpr int SC = 4 * NOUT;                   // TMEM columns of a stage (four rows)
+    static constexpr int TCOLS = SC * 2 <= 32 ? 32 : (SC * 2 <= 64 ? 64 : (SC * 2 <= 128 ? 128 : 256));
+    static constexpr size_t smem() {
+        return (size_t)NSLICE * WSL + ZERO + (size_t)NS * SLOT + (2 * NS + 4) * 8 + 16;
     }
 };
 
@@ -192,23 +202,24 @@ __device__ __forceinline__ bool ws_wait(uint64_t *mbar, uint32_t parity, volatil
     return false;
 }
 
-template <int CIN, int NOUT, int EPI, int R>
+template <int CIN, int NOUT, int EPI>
 __global__ void __launch_bounds__(192)
 conv3x3_ws(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt,
            const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ Y,
            float *__restrict__ Yf, int H, int W, int rows, int *err) {
-    using WC = WsConv<CIN, R>;
+    using WC = WsConv<CIN, NOUT>;
     constexpr int KPS = ConvK<CIN>::KP;
-    constexpr int KR = WC::KR, NMMA = KR / 16, CB = WC::CB, CBS = WC::CBS, SLOT = WC::SLOT;
-    constexpr int NS = WC::NS, NACC = WC::NACC;
+    constexpr int CB = WC::CB, CBS = WC::CBS, SLOT = WC::SLOT, NSLICE = WC::NSLICE, WSL = WC::WSL;
+    constexpr int NS = WC::NS, SC = WC::SC;
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sb = sm;                                   // NOUT x KR weights
-    unsigned char *slots = sm + NOUT * KR * 2;                // NS x SLOT
+    unsigned char *sw = sm;                                   // NSLICE x WSL weight arrays
+    unsigned char *zero = sw + NSLICE * WSL;                  // zero tile
+    unsigned char *slots = zero + WC::ZERO;                   // NS x SLOT
     uint64_t *full = reinterpret_cast<uint64_t *>(slots + NS * SLOT);
     uint64_t *freed = full + NS;
     uint64_t *accf = freed + NS;
-    uint64_t *acce = accf + NACC;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + NACC);
+    uint64_t *acce = accf + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int x0 = blockIdx.x * 128, ya = blockIdx.y * rows, img = blockIdx.z;
@@ -216,31 +227,36 @@ conv3x3_ws(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict_
     const int nin = nrows + 2;
     const size_t plane = (size_t)H * W;
 
-    for (int i = t; i < NOUT * (KR / 8); i += blockDim.x) {
-        const int r = i / (KR / 8), kb = i % (KR / 8);
+    // weights: slice s, block blk (row tap dyi = 2 - blk), output channel co,
+    // 16-channel K chunk kc of 8
+    for (int i = t; i < NSLICE * 3 * NOUT * 2; i += blockDim.x) {
+        const int kc = i & 1, n = (i >> 1) % (3 * NOUT), sl = (i >> 1) / (3 * NOUT);
+        const int blk = n / NOUT, co = n % NOUT, dyi = 2 - blk;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (CIN == 8) {
-            const int dyi = kb / 4, dxs = kb % 4;
-            if (dxs < 3) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KPS + (dyi * 3 + dxs) * 8);
+            const int dx = 2 * sl + kc;
+            if (dx < 3) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)co * KPS + (dyi * 3 + dx) * 8);
         } else {
-            v = *reinterpret_cast<const uint4 *>(Wt + (size_t)r * KPS + kb * 8);
+            const int dx = sl >> 1, h = sl & 1;
+            v = *reinterpret_cast<const uint4 *>(Wt + (size_t)co * KPS + (dyi * 3 + dx) * CIN + h * 16 + kc * 8);
         }
-        *reinterpret_cast<uint4 *>(sb + kmajor_off(r, kb * 8, NOUT)) = v;
+        *reinterpret_cast<uint4 *>(sw + sl * WSL + kmajor_off(n, kc * 8, 3 * NOUT)) = v;
     }
-    // zero the slots: pixels outside the image are never written again
-    for (int i = t; i < NS * SLOT / 16; i += blockDim.x)
-        reinterpret_cast<uint4 *>(slots)[i] = make_uint4(0, 0, 0, 0);
+    // zero tile and slots: pixels outside the image are never written again
+    for (int i = t; i < (WC::ZERO + NS * SLOT) / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(zero)[i] = make_uint4(0, 0, 0, 0);
     fence_async_smem();
     if (warp == 0) tmem_alloc(tslot, WC::TCOLS);
     if (t == 0) {
         for (int q = 0; q < NS; ++q) { mbar_init(&full[q], 1); mbar_init(&freed[q], 1); }
-        for (int a = 0; a < NACC; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 4); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 4); }
         *abort = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    const int nbatch = (nrows + 3) / 4;
 
     if (warp == 4) {
         if (lane == 0) {
@@ -251,7 +267,7 @@ conv3x3_ws(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict_
             for (; q < nin; ++q) {
                 const int sl = q % NS, yy = ya - 1 + q;
                 if (q >= NS && !(ok = ws_wait(&freed[sl], (uint32_t)((q / NS) - 1) & 1u, abort, true))) break;
-                if (yy < 0 || yy >= H) {      // not loaded: its taps are skipped
+                if (yy < 0 || yy >= H) {      // not loaded: its MMAs are not issued
                     mbar_arrive(&full[sl]);
                     continue;
                 }
@@ -267,91 +283,102 @@ conv3x3_ws(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict_
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            int landed = 0, issued = 0;
-            bool ok = true;
-            for (int j0 = 0; j0 < nrows && ok; j0 += R) {
-                const int nb = min(R, nrows - j0);
+            int landed = 0, freed_rows = 0;
+            bool ok = true, any = false;
+            const uint64_t zd = smem_desc(smem_u32(zero), 128 * 16, 128);
+            for (int b = 0; b < nbatch && ok; ++b) {
+                const int j0 = 4 * b, nb = min(4, nrows - j0), st = b & 1;
                 while (ok && landed < j0 + nb + 2) {
                     ok = ws_wait(&full[landed % NS], (uint32_t)(landed / NS) & 1u, abort, true);
                     if (ok) ++landed;
                 }
-                for (int r = 0; r < nb && ok; ++r) {
-                    const int j = j0 + r;
-                    if (j >= NACC) ok = ws_wait(&acce[j % NACC], (uint32_t)((j / NACC) - 1) & 1u, abort, true);
-                }
+                if (ok && b >= 2) ok = ws_wait(&acce[st], (uint32_t)((b / 2) - 1) & 1u, abort, true);
                 if (!ok) break;
                 tc_fence_after();
-                unsigned started = 0;   // bit r: row j0 + r has its first MMA
+                const uint32_t dst = tmem + st * SC;
+                mma_bf16(dst, zd, zd, idesc_bf16_f32(SC), 0u);
 #pragma unroll 1
-                for (int m = 0; m < NMMA; ++m) {
-                    uint32_t aoff, lbo, dyi;
-                    if (CIN == 8) {
-                        dyi = m / 2;
-                        aoff = (m % 2) * 2 * 16;
-                        lbo = 16;
-                    } else {
-                        const int tap = m / 2;
-                        dyi = tap / 3;
-                        aoff = (m % 2) * 2 * CBS + (tap % 3) * 16;
-                        lbo = CBS;
-                    }
-                    const uint64_t bd = smem_desc(smem_u32(sb) + m * NOUT * 32, NOUT * 16, 128);
-                    for (int r = 0; r < nb; ++r) {
-                        const int j = j0 + r, y = ya + j;
-                        if ((dyi == 0 && y == 0) || (dyi == 2 && y == H - 1)) continue;   // row outside the image
-                        const uint64_t ad = smem_desc(smem_u32(slots + ((j + dyi) % NS) * SLOT) + aoff, lbo, 128);
-                        mma_bf16(tmem + (j % NACC) * 32, ad, bd, idesc_bf16_f32(NOUT), (started >> r) & 1u);
-                        started |= 1u << r;
+                for (int yi = 0; yi < nb + 2; ++yi) {
+                    const int q = j0 + yi, yy = ya - 1 + q;
+                    if (yy < 0 || yy >= H) continue;
+                    const int r_lo = max(0, yi - 2), r_hi = min(nb - 1, yi);
+                    if (r_lo > r_hi) continue;
+                    const int cnt = r_hi - r_lo + 1, off = 2 - (yi - r_lo);   // first block: row tap yi - r_lo
+                    const uint32_t slot = smem_u32(slots + (q % NS) * SLOT);
+#pragma unroll
+                    for (int sl = 0; sl < NSLICE; ++sl) {
+                        uint32_t aoff, lbo;
+                        if (CIN == 8) { aoff = sl * 2 * 16; lbo = 16; }
+                        else { aoff = (sl & 1) * 2 * CBS + (sl >> 1) * 16; lbo = CBS; }
+                        const uint64_t ad = smem_desc(slot + aoff, lbo, 128);
+                        const uint64_t bd = smem_desc(smem_u32(sw + sl * WSL) + off * NOUT * 16, 3 * NOUT * 16, 128);
+                        mma_bf16(dst + r_lo * NOUT, ad, bd, idesc_bf16_f32(cnt * NOUT), 1u);
                     }
                 }
-                for (int r = 0; r < nb; ++r) {
-                    mma_commit(&accf[(j0 + r) % NACC]);
-                    mma_commit(&freed[(j0 + r) % NS]);
-                }
-                issued = j0 + nb;
+                mma_commit(&accf[st]);
+                // input rows no later batch reads: q < j0 + nb (the next batch starts at row j0 + 4)
+                for (; freed_rows < j0 + nb; ++freed_rows) mma_commit(&freed[freed_rows % NS]);
+                any = true;
             }
             if (!ok) atomicOr(err, 1);
             // MMAs in flight must finish before the tensor memory is freed
-            if (issued > 0) {
-                const int jl = issued - 1;
+            if (any) {
+                const int jl = freed_rows - 1;
                 ws_wait(&freed[jl % NS], (uint32_t)(jl / NS) & 1u, abort, false);
             }
         }
     } else {
-        for (int j = 0; j < nrows; ++j) {
-            const int a = j % NACC;
-            if (!ws_wait(&accf[a], (uint32_t)(j / NACC) & 1u, abort, true)) {
+        for (int b = 0; b < nbatch; ++b) {
+            const int j0 = 4 * b, nb = min(4, nrows - j0), st = b & 1;
+            if (!ws_wait(&accf[st], (uint32_t)(b / 2) & 1u, abort, true)) {
                 if (lane == 0) atomicOr(err, 1);
                 break;
             }
             tc_fence_after();
-            float v[32];
-            tmem_ld32(tmem + a * 32 + ((uint32_t)(warp * 32) << 16), v);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[a]);
-            const int p = warp * 32 + lane, xx = x0 + p, y = ya + j;
-            if (xx >= W) continue;
-            if (EPI == EPI_OUT) {
-                const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
-                const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * 8 + 6);
-                Yf[pix] = __high2float(pm) * (v[0] + bias[0] + __low2float(pm));
-            } else {
-                __align__(16) __nv_bfloat16 o[32];
-                if (EPI == EPI_RELU) {
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(fmaxf(v[jj] + bias[jj], 0.f));
+            const int p = warp * 32 + lane, xx = x0 + p;
+            for (int r = 0; r < nb; ++r) {
+                const uint32_t ta = tmem + st * SC + r * NOUT + ((uint32_t)(warp * 32) << 16);
+                const int y = ya + j0 + r;
+                if (NOUT == 16) {
+                    float v[16];
+                    tmem_ld16(ta, v);
+                    if (r == nb - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acce[st]);
+                    }
+                    if (xx < W && EPI == EPI_OUT) {
+                        const size_t pix = (size_t)img * plane + (size_t)y * W + xx;
+                        const __nv_bfloat162 pm = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * 8 + 6);
+                        Yf[pix] = __high2float(pm) * (v[0] + bias[0] + __low2float(pm));
+                    }
                 } else {
-                    __align__(16) __nv_bfloat16 mk[32];
+                    float v[32];
+                    tmem_ld32(ta, v);
+                    if (r == nb - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acce[st]);
+                    }
+                    if (xx >= W) continue;
+                    __align__(16) __nv_bfloat16 o[32];
+                    if (EPI == EPI_RELU) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(fmaxf(v[jj] + bias[jj], 0.f));
+                    } else {
+                        __align__(16) __nv_bfloat16 mk[32];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            reinterpret_cast<uint4 *>(mk)[q] =
+                                *reinterpret_cast<const uint4 *>(mask + act_off(img, y, xx, q, 32, H, W));
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            o[jj] = __float2bfloat16(__bfloat162float(mk[jj]) > 0.f ? v[jj] : 0.f);
+                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        reinterpret_cast<uint4 *>(mk)[q] = *reinterpret_cast<const uint4 *>(mask + act_off(img, y, xx, q, 32, H, W));
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) o[jj] = __float2bfloat16(__bfloat162float(mk[jj]) > 0.f ? v[jj] : 0.f);
+                        *reinterpret_cast<uint4 *>(Y + act_off(img, y, xx, q, 32, H, W)) = reinterpret_cast<uint4 *>(o)[q];
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<uint4 *>(Y + act_off(img, y, xx, q, 32, H, W)) = reinterpret_cast<uint4 *>(o)[q];
             }
         }
     }
@@ -708,17 +735,14 @@ cudaError_t salloc(swe_surrogate *s, void **p, size_t bytes) {
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
-constexpr int kConvR = 2;   // output rows whose MMA chains run together
-
 template <int CIN, int NOUT, int EPI>
 cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, const __nv_bfloat16 *Wt, const float *bias,
                  const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B) {
     (void)l;
-    using WC = WsConv<CIN, kConvR>;
-    auto kern = conv3x3_ws<CIN, NOUT, EPI, kConvR>;
+    using WC = WsConv<CIN, NOUT>;
+    auto kern = conv3x3_ws<CIN, NOUT, EPI>;
     // enough shared memory that the CTAs of one SM fit its 512 TMEM columns
-    static const size_t smem =
-        std::max<size_t>(WC::template smem<NOUT>(), (size_t)(227 * 1024) / (512 / WC::TCOLS) - 1024);
+    static const size_t smem = std::max<size_t>(WC::smem(), (size_t)(227 * 1024) / (512 / WC::TCOLS) - 1024);
     static int resident = 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -735,10 +759,10 @@ cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, con
         resident = std::max(1, per_sm) * sms;
     }
     // one wave: the column bands x images share the resident CTAs, each CTA
-    // streams a run of rows (at least 8, to amortise its set-up)
+    // streams a run of rows (a multiple of 4, at least 8, to amortise its set-up)
     const int bands = (s->T + 127) / 128;
     const int groups = std::max(1, resident / (bands * B));
-    const int rows = std::max(8, (s->T + groups - 1) / groups);
+    const int rows = std::max(8, ((s->T + groups - 1) / groups + 3) / 4 * 4);
     dim3 grid(bands, (s->T + rows - 1) / rows, B);
     kern<<<grid, 192, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
     return cudaGetLastError();
