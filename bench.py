@@ -623,14 +623,14 @@ def main():
     ap.add_argument("--sur-train-seconds", type=float, default=30.0)
     ap.add_argument("--sur-lr", type=float, default=1e-3)
     ap.add_argument("--sur-windows", type=int, default=40)
-    ap.add_argument("--sur-f", type=int, default=10)
-    ap.add_argument("--sur-judge", type=int, default=10)
+    ap.add_argument("--sur-f", type=int, default=25)
+    ap.add_argument("--sur-judge", type=int, default=20)
     ap.add_argument("--sur-bound", type=float, default=0.5)
     ap.add_argument("--sur-loss", default="l1", choices=["mse", "l1"])
     ap.add_argument("--sur-gap", type=int, default=1, help="windows skipped between training samples")
     ap.add_argument("--sur-val", type=int, default=80, help="held-out validation samples (tiles)")
     ap.add_argument("--sur-val-points", type=int, default=6)
-    ap.add_argument("--sur-variants", default="10:20,25:20,50:20",
+    ap.add_argument("--sur-variants", default="10:10,10:20,50:20",
                     help="extra f:judge_every evaluations of the trained network")
     args = ap.parse_args()
     if args.impl == "reference":
