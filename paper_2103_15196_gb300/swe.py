@@ -465,7 +465,7 @@ class Surrogate:
     def apply(self, solver):
         self._check(self._L.swe_surrogate_apply(self._h, solver._h))
 
-    def run(self, solver, nwindows, K=50, f=10, judge_every=10, bound=0.02, stats=None):
+    def run(self, solver, nwindows, K=50, f=25, judge_every=20, bound=0.5, stats=None):
         st = stats if stats is not None else SurrogateStats()
         self._check(self._L.swe_surrogate_run(self._h, solver._h, int(nwindows), int(K), int(f), int(judge_every),
                                               float(bound), ctypes.byref(st)))
