@@ -505,13 +505,15 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
         else CellIO<T>::load(in, kk, H, Hu, Hv, b);
     }
 
-    template <int P> __device__ __forceinline__ void pos(int s) {
+    // FULL: every stage's row is inside the strip (s in [y0 + 5, y1 + 3]), so
+    // the row-range tests are dropped (the same arithmetic, fewer branches).
+    template <int P, bool FULL> __device__ __forceinline__ void pos(int s) {
         constexpr int P4 = P & 3, PM1_4 = (P + 3) & 3, PM2_4 = (P + 2) & 3, PM3_4 = (P + 1) & 3,
                       PM4_4 = P & 3, PM5_4 = (P + 3) & 3;
         constexpr int PM3_2 = (P + 1) & 1, PM4_2 = P & 1, PM5_2 = (P + 1) & 1;
         T v_s = T(0);
         // ---------------- load row s (ghost rows by even extension)
-        if (s >= y0 - 4 && s <= y1 + 3) {
+        if (FULL || (s >= y0 - 4 && s <= y1 + 3)) {
             const T H = aH, Hu = aHu, Hv = aHv, bb = ab;
             const T syT = T(asy);
             aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
@@ -528,12 +530,12 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             S.v[P4][o] = v_s;
         }
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
-        if (s - 1 >= y0 - 3 && s - 1 <= y1 + 2) {
+        if (FULL || (s - 1 >= y0 - 3 && s - 1 <= y1 + 2)) {
             const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - S.v[PM2_4][o]));
             S.Hh[PM1_4][o] = Hr<P, 1>()[o] / A;
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
-        if (s - 2 >= y0 - 2 && s - 2 <= y1 + 1) {
+        if (FULL || (s - 2 >= y0 - 2 && s - 2 <= y1 + 1)) {
             const int r = s - 2;
             const T Hc = Hr<P, 2>()[o];
             const bool wet = is_wet(Hc, c);
@@ -578,7 +580,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             S.jx[PM2_4][o] = jx; S.jy[PM2_4][o] = jy; S.ja[PM2_4][o] = ja;
         }
         // ---------------- K8: update row s-5
-        if (s - 5 >= y0 && s - 5 <= y1 - 1 && out_lane) {
+        if ((FULL || (s - 5 >= y0 && s - 5 <= y1 - 1)) && out_lane) {
             const int r = s - 5;
             const T Hc = Hr<P, 5>()[o], bc = Br<P, 5>()[o];
             bool src = false;
@@ -599,7 +601,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
         }
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
-        if (s - 4 >= y0 && s - 4 <= y1 - 1) {
+        if (FULL || (s - 4 >= y0 && s - 4 <= y1 - 1)) {
             const bool wc = is_wet(Hr<P, 4>()[o], c), we = is_wet(Hr<P, 4>()[o + 1], c);
             T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
             if (wc || we) {
@@ -614,7 +616,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
         }
         // ---------------- per-cell limited face states (K7 reconstruction), row s-3,
         // and the y-face (s-4 | s-3)
-        if (s - 3 >= y0 - 1 && s - 3 <= y1) {
+        if (FULL || (s - 3 >= y0 - 1 && s - 3 <= y1)) {
             const T H0 = Hr<P, 3>()[o], b0 = Br<P, 3>()[o];
             const T Hm = Hr<P, 3>()[o - 1], Hp = Hr<P, 3>()[o + 1];
             const T Hs = Hr<P, 4>()[o], Hn = Hr<P, 2>()[o];
@@ -637,14 +639,14 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
                 cell_faces<T>(S.uy[PM4_4][o], S.uy[PM3_4][o], S.uy[PM2_4][o], qS[2], hn5[2]);
                 cell_faces<T>(S.wx[PM4_4][o], S.wx[PM3_4][o], S.wx[PM2_4][o], qS[3], hn5[3]);
                 cell_faces<T>(S.wy[PM4_4][o], S.wy[PM3_4][o], S.wy[PM2_4][o], qS[4], hn5[4]);
-                if (s - 3 >= y0 && (ws || w0))
+                if ((FULL || s - 3 >= y0) && (ws || w0))
                     face_flux2<T>(c, k, qN, qS, ws, w0, S.uy[PM4_4][o], S.uy[PM3_4][o], S.jy[PM4_4][o],
                                   S.jy[PM3_4][o], S.ja[PM4_4][o], S.ja[PM3_4][o], Br<P, 4>()[o], b0,
                                   G[0], G[1], G[2], G[3]);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) qN[q] = hn5[q];
             }
-            if (s - 3 >= y0) {
+            if (FULL || s - 3 >= y0) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) { G2[q] = G1[q]; G1[q] = G[q]; }
             }
@@ -727,10 +729,17 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     // sweep positions y0-8 .. y1+4 in groups of 4 (y0 is a multiple of 8)
     for (int s = y0 - 8; s <= y1 + 4; s += 4) {
         w.set_banks(s);
-        w.template pos<0>(s);
-        w.template pos<1>(s + 1);
-        w.template pos<2>(s + 2);
-        w.template pos<3>(s + 3);
+        if (s >= y0 + 5 && s + 3 <= y1 + 3) {
+            w.template pos<0, true>(s);
+            w.template pos<1, true>(s + 1);
+            w.template pos<2, true>(s + 2);
+            w.template pos<3, true>(s + 3);
+        } else {
+            w.template pos<0, false>(s);
+            w.template pos<1, false>(s + 1);
+            w.template pos<2, false>(s + 2);
+            w.template pos<3, false>(s + 3);
+        }
     }
     block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
 }
