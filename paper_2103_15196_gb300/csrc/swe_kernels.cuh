@@ -164,54 +164,6 @@ __device__ inline T axis_force(const K<T> &k, T ec, T ratio, T eta_p, T b_p, boo
     return -(k.coef * (ep - em)) * ratio;
 }
 
-// Limited piecewise-linear face states from the cells m, c, e, p around the
-// face c|e: left state from c, right state from e.
-template <typename T> __device__ inline void recon(const T f[4], T &L, T &R) {
-    T sc = minmod(f[1] - f[0], f[2] - f[1]);
-    T se = minmod(f[2] - f[1], f[3] - f[2]);
-    L = f[1] + T(0.5) * sc;
-    R = f[2] - T(0.5) * se;
-}
-
-// Fluxes through one face from the four cells m, c, e, p along its normal:
-// H, eta (free surface), un (normal transport velocity), wx, wy (end
-// velocity), plus the cell-centred Grass loads and beds of c and e.
-// Returns mass, x-momentum, y-momentum and Exner fluxes.
-template <typename T>
-__device__ inline void face_flux(const SweConst &c, const K<T> &k,
-                                 const T H[4], const T eta[4], const T un[4], const T wx[4], const T wy[4],
-                                 bool wet_c, bool wet_e, T Jn_c, T Jn_e, T Ja_c, T Ja_e, T b_c, T b_e,
-                                 T &Fm, T &Fx, T &Fy, T &Fj) {
-    T qL[5], qR[5];
-    recon<T>(H, qL[0], qR[0]);
-    recon<T>(eta, qL[1], qR[1]);
-    recon<T>(un, qL[2], qR[2]);
-    recon<T>(wx, qL[3], qR[3]);
-    recon<T>(wy, qL[4], qR[4]);
-    // hydrostatic face depths
-    T bL = qL[1] - qL[0], bR = qR[1] - qR[0];
-    T bf = bL > bR ? bL : bR;
-    T HL = qL[1] - bf, HR = qR[1] - bf;
-    if (!(HL > T(0))) HL = T(0);
-    if (!(HR > T(0))) HR = T(0);
-    T uL = qL[2], uR = qR[2];
-    T cL = wet_c ? mm_sqrt(k.g * HL) : T(0);
-    T cR = wet_e ? mm_sqrt(k.g * HR) : T(0);
-    T aL = uL - cL, aR = uR - cR, pL = uL + cL, pR = uR + cR;
-    T sL = aL < aR ? aL : aR, sR = pL > pR ? pL : pR;
-    Fm = hll(HL, HR, HL * uL, HR * uR, sL, sR);
-    T UxL = HL * qL[3], UxR = HR * qR[3];
-    Fx = hll(UxL, UxR, UxL * uL, UxR * uR, sL, sR);
-    T UyL = HL * qL[4], UyR = HR * qR[4];
-    Fy = hll(UyL, UyR, UyL * uL, UyR * uR, sL, sR);
-    Fj = T(0);
-    if (c.sediment_on) {
-        T su = un[1] + un[2];
-        T Jadv = su > T(0) ? Jn_c : (su < T(0) ? Jn_e : T(0));
-        Fj = Jadv - (k.cjh * (Ja_c + Ja_e)) * (b_e - b_c);
-    }
-}
-
 template <typename T> __device__ inline unsigned long long max_bits(T x);
 template <> __device__ inline unsigned long long max_bits<float>(float x) { return (unsigned long long)__float_as_uint(x); }
 template <> __device__ inline unsigned long long max_bits<double>(double x) { return (unsigned long long)__double_as_longlong(x); }
