@@ -44,6 +44,25 @@ def _dist():
     return rank, world, local
 
 
+def _max_over_ranks(x, world):
+    """The largest value of x over all ranks (x itself on one rank); NCCL
+    reduces device tensors, gloo host tensors."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _aggregate_rate(cells_per_step, steps, seconds, world):
+    """Whole-job Gcell/s: the cell updates of all ranks over the slowest
+    rank's time (each rank runs the same workload: weak scaling)."""
+    return float(cells_per_step) * steps * world / seconds / 1e9
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -507,16 +526,10 @@ def run_ours(args):
         ev1.synchronize()
     torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = _max_over_ranks(ev0.elapsed_time(ev1), world)
     S.sync()
     d1 = S.diag()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    cells = float(n) * n * K * world
-    value = cells / (ms * 1e-3) / 1e9
+    value = _aggregate_rate(float(n) * n, K, ms * 1e-3, world)
     comp = d1["cells_computed"] - d0["cells_computed"]
     copied = d1["cells_copied"] - d0["cells_copied"]
     alg_bytes_launch = BYTES_PER_CELL * (comp + copied) / K
@@ -538,13 +551,8 @@ def run_ours(args):
         S.get_state(out=host_out)
         t1 = time.perf_counter()
         barrier()
-        el = t1 - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": float(n) * n * Ke * world / el / 1e9, "unit": UNIT,
+        el = _max_over_ranks(t1 - t0, world)
+        e2e = {"value": _aggregate_rate(float(n) * n, Ke, el, world), "unit": UNIT,
                "h2d_bytes_per_step": int(4 * n * n * 4 / Ke), "d2h_bytes_per_step": int(4 * n * n * 4 / Ke),
                "steps": Ke, "seconds": el}
     dd = S.diag()
@@ -616,7 +624,7 @@ def main():
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--surrogate-only", action="store_true", help="run only the config-5 surrogate experiment")
+    ap.add_argument("--surrogate-only", action="store_true", help="run only the learned bed surrogate experiment")
     ap.add_argument("--sur-samples", type=int, default=2000)
     ap.add_argument("--sur-snaps-per-run", type=int, default=25)
     ap.add_argument("--sur-spin", type=int, default=300)
