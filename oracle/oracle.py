@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("dt_literal_D", ctypes.c_int), ("hgs_skip", ctypes.c_int),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("frozen_hydro", ctypes.c_int), ("neg_tol", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
     ]
 
 
@@ -55,8 +56,8 @@ class _DtTerms(ctypes.Structure):
 
 class _StepInfo(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("binding", ctypes.c_int),
-                ("inflow_vol", ctypes.c_double), ("n_negative", ctypes.c_long),
-                ("n_bad", ctypes.c_long), ("active_tiles", ctypes.c_long)]
+                ("inflow_vol", ctypes.c_double), ("rain_vol", ctypes.c_double), ("outflow_vol", ctypes.c_double),
+                ("n_negative", ctypes.c_long), ("n_bad", ctypes.c_long), ("active_tiles", ctypes.c_long)]
 
 
 @dataclass
@@ -84,9 +85,15 @@ class Params:
     tile_y: int = 64
     frozen_hydro: int = 0
     neg_tol: float = 1e-10
+    bc_w: int = 0           # boundary kinds: 0 reflective wall, 1 open (zero-gradient)
+    bc_e: int = 0
+    bc_s: int = 0
+    bc_n: int = 0
 
     def c(self) -> _Params:
-        return _Params(**asdict(self))
+        d = asdict(self)
+        bc = [d.pop(k) for k in ("bc_w", "bc_e", "bc_s", "bc_n")]
+        return _Params(**d, bc=(ctypes.c_int * 4)(*bc))
 
 
 _lib = None
@@ -99,14 +106,14 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         u8 = ctypes.POINTER(ctypes.c_uint8)
         L.orc_step.restype = ctypes.c_long
-        L.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp,
+        L.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp,
                                ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                dp, dp, dp, dp, ctypes.POINTER(_StepInfo)]
         L.orc_step_rect.restype = ctypes.c_long
-        L.orc_step_rect.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp,
+        L.orc_step_rect.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp,
                                     ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                    dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long)]
+                                    dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long), dp]
         L.orc_dt_terms.restype = ctypes.c_int
         L.orc_dt_terms.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, ctypes.POINTER(_DtTerms)]
         L.orc_dt.restype = ctypes.c_double
@@ -171,6 +178,8 @@ class StepInfo:
     n_negative: int
     n_bad: int
     active_tiles: int
+    rain_vol: float = 0.0
+    outflow_vol: float = 0.0
 
 
 def _prep(p: Params, st: State, n, src, qb):
@@ -190,9 +199,14 @@ def _prep(p: Params, st: State, n, src, qb):
 
 
 def step(p: Params, st: State, n, src=None, qb=None, hydro: Hydrograph | None = None,
-         t: float = 0.0, t_end: float = -1.0):
-    """One full step (K1..K8).  Returns (new State, StepInfo)."""
+         t: float = 0.0, t_end: float = -1.0, rain=None):
+    """One full step (K1..K8).  rain: per-cell water source in m/s (or None).
+    Returns (new State, StepInfo)."""
     H, Hu, Hv, b, n, src, srcp, qb, qbp = _prep(p, st, n, src, qb)
+    rainp = None
+    if rain is not None:
+        rain = _f64(np.broadcast_to(rain, H.shape), H.shape)
+        rainp = _d(rain)
     out = [np.empty_like(H) for _ in range(4)]
     info = _StepInfo()
     pc = p.c()
@@ -200,10 +214,10 @@ def step(p: Params, st: State, n, src=None, qb=None, hydro: Hydrograph | None = 
         nk, tk, Qk = len(hydro.t), _d(hydro.t), _d(hydro.Q)
     else:
         nk, tk, Qk = 0, None, None
-    lib().orc_step(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp,
+    lib().orc_step(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, rainp,
                    nk, tk, Qk, t, t_end, *(_d(o) for o in out), ctypes.byref(info))
     return State(*out), StepInfo(info.dt, info.binding, info.inflow_vol, info.n_negative,
-                                 info.n_bad, info.active_tiles)
+                                 info.n_bad, info.active_tiles, info.rain_vol, info.outflow_vol)
 
 
 def step_rect(p: Params, st: State, n, dt: float, rect, src=None, qb=None, dHs: float = 0.0):
@@ -214,8 +228,8 @@ def step_rect(p: Params, st: State, n, dt: float, rect, src=None, qb=None, dHs: 
     out = [np.zeros_like(H) for _ in range(4)]
     nneg = ctypes.c_long(0)
     pc = p.c()
-    bad = lib().orc_step_rect(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp,
-                              dHs, dt, x0, y0, x1, y1, *(_d(o) for o in out), ctypes.byref(nneg))
+    bad = lib().orc_step_rect(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, None,
+                              dHs, dt, x0, y0, x1, y1, *(_d(o) for o in out), ctypes.byref(nneg), None)
     return [o[y0:y1, x0:x1].copy() for o in out], bad
 
 
@@ -255,13 +269,13 @@ def hll(UL, UR, FL, FR, sL, sR):
 
 
 def run(p: Params, st: State, n, nsteps: int, src=None, qb=None, hydro=None, t: float = 0.0,
-        t_end: float = -1.0, on_step=None):
+        t_end: float = -1.0, on_step=None, rain=None):
     """Advances nsteps (or until t_end).  Returns (State, t, list of StepInfo)."""
     infos = []
     for _ in range(nsteps):
         if t_end > 0 and t >= t_end:
             break
-        st, info = step(p, st, n, src=src, qb=qb, hydro=hydro, t=t, t_end=t_end)
+        st, info = step(p, st, n, src=src, qb=qb, hydro=hydro, t=t, t_end=t_end, rain=rain)
         t = t_end if info.binding == 4 else t + info.dt   # a clipped step lands on t_end
         infos.append(info)
         if on_step is not None:

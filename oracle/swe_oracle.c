@@ -56,6 +56,7 @@ typedef struct {
     int tile_x, tile_y;  /* HGS block size L x K */
     int frozen_hydro;    /* test hook: hydro state frozen, only b evolves */
     double neg_tol;      /* H' < -neg_tol is reported as a numerical failure */
+    int bc[4];           /* boundary of the W, E, S, N sides: 0 reflective wall, 1 open */
 } orc_params;
 
 typedef struct {
@@ -68,6 +69,8 @@ typedef struct {
     double dt;          /* step taken */
     int binding;        /* 0: h/(2vp), 1: h/vs, 2: h^2/(2D), 3: dt_max, 4: t_end clip */
     double inflow_vol;  /* water volume added by sources during the step */
+    double rain_vol;    /* water volume added by the per-cell source (rain) */
+    double outflow_vol; /* water volume that left through open boundaries */
     long n_negative;    /* cells with H' < 0 */
     long n_bad;         /* cells with H' < -neg_tol or a non-finite result */
     long active_tiles;  /* tiles computed (HGS) */
@@ -75,16 +78,28 @@ typedef struct {
 
 /* ---------------------------------------------------------------- helpers */
 
-/* Even extension of index i onto [0, n): reflection across both walls.
- * sign = -1 when an odd number of reflections was taken (normal component flips). */
-static int ext_index(int i, int n, double *sign)
+/* Ghost index of i for the boundaries below 0 (lo_open) and at n (hi_open):
+ * a reflective wall is the even (mirror) extension, the normal momentum
+ * changing sign on every reflection; an open boundary repeats its boundary
+ * cell, momentum unchanged (zero-gradient outflow, READING: the paper names
+ * no outflow condition).  Walls on both sides give the 2n-periodic even
+ * extension. */
+static int ext_index(int i, int n, int lo_open, int hi_open, double *sign)
 {
-    int period = 2 * n;
-    int p = i % period;
-    if (p < 0) p += period;
-    if (p < n) { *sign = 1.0; return p; }
-    *sign = -1.0;
-    return period - 1 - p;
+    double s = 1.0;
+    for (;;) {
+        if (i < 0) {
+            if (lo_open) { i = 0; break; }
+            i = -1 - i; s = -s;
+        } else if (i >= n) {
+            if (hi_open) { i = n - 1; break; }
+            i = 2 * n - 1 - i; s = -s;
+        } else {
+            break;
+        }
+    }
+    *sign = s;
+    return i;
 }
 
 /* minmod TVD limiter (READING: the paper names "TVD-limiters" without the law). */
@@ -257,13 +272,16 @@ static double *xalloc(long n) { return (double *)calloc((size_t)n, sizeof(double
 /* Computes state^{n+1} on [x0,x1) x [y0,y1) from state^n, for a given dt and a
  * given source depth increment dHs (added to source-flagged cells).  Writes
  * only the rectangle of the full-size output arrays.  qb (nullable) is the
- * per-cell bed source q_b^+ - q_b^- of Eq. 1.  Returns the number of cells
- * with H' < -neg_tol or a non-finite result; *nneg counts H' < 0. */
+ * per-cell bed source q_b^+ - q_b^- of Eq. 1; rain (nullable) a per-cell
+ * water source sigma of Eq. 6 row 1 in m/s (rain > 0, evaporation < 0).
+ * Returns the number of cells with H' < -neg_tol or a non-finite result;
+ * *nneg counts H' < 0; *outflow (nullable) gets the volume of water that
+ * left the grid through the rectangle's part of the domain boundary. */
 long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
                    const double *Hv, const double *b, const double *nman,
-                   const uint8_t *src, const double *qb, double dHs, double dt,
+                   const uint8_t *src, const double *qb, const double *rain, double dHs, double dt,
                    int x0, int y0, int x1, int y1,
-                   double *Ho, double *Huo, double *Hvo, double *bo, long *nneg)
+                   double *Ho, double *Huo, double *Hvo, double *bo, long *nneg, double *outflow)
 {
     const int R = ORC_R;
     ext_t e;
@@ -277,12 +295,14 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
     e.Jx = xalloc(NE); e.Jy = xalloc(NE); e.Ja = xalloc(NE); e.cf = xalloc(NE);
     double *eta = xalloc(NE), *etah = xalloc(NE);
 
-    /* ghost fill (walls: even extension, normal momentum negated) and cell
+    /* ghost fill (walls: even extension, normal momentum negated; open
+     * sides: the boundary cell repeated) and cell
      * velocities v = (Hu, Hv)/H for wet cells, v = 0 for dry cells */
     for (int j = y0 - R; j < y1 + R; ++j)
         for (int i = x0 - R; i < x1 + R; ++i) {
             double sx, sy;
-            int ii = ext_index(i, p->nx, &sx), jj = ext_index(j, p->ny, &sy);
+            int ii = ext_index(i, p->nx, p->bc[0], p->bc[1], &sx);
+            int jj = ext_index(j, p->ny, p->bc[2], p->bc[3], &sy);
             long k = (long)jj * p->nx + ii, c = E(&e, i, j);
             double h = H[k];
             e.H[c] = h; e.b[c] = b[k]; e.n[c] = nman[k];
@@ -437,6 +457,7 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
             if (!p->frozen_hydro) {
                 hn = e.H[c] - dtdx * ((FX[0][fe] - FX[0][fw]) + (FY[0][fn] - FY[0][fs]));
                 if (src && src[k]) hn = hn + dHs;
+                if (rain) hn = hn + dt * rain[k];
                 hun = e.H[c] * e.wx[c] - dtdx * ((FX[1][fe] - FX[1][fw]) + (FY[1][fn] - FY[1][fs]));
                 hvn = e.H[c] * e.wy[c] - dtdx * ((FX[2][fe] - FX[2][fw]) + (FY[2][fn] - FY[2][fs]));
                 if (!(hn > p->eps_wet)) { hun = 0.0; hvn = 0.0; }
@@ -450,6 +471,20 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
             if (!(hn >= -p->neg_tol) || !isfinite(hn) || !isfinite(bn) || !isfinite(hun) || !isfinite(hvn)) ++bad;
         }
     if (nneg) *nneg = neg;
+    if (outflow) {
+        /* mass fluxes through the domain's boundary faces (zero at walls) */
+        double out = 0.0, ah = dt * p->dx;
+        for (int j = y0; j < y1; ++j) {
+            long r = (long)(j - y0) * FW;
+            if (x0 == 0) out -= ah * FX[0][r];
+            if (x1 == p->nx) out += ah * FX[0][r + (x1 - x0)];
+        }
+        for (int i = x0; i < x1; ++i) {
+            if (y0 == 0) out -= ah * FY[0][i - x0];
+            if (y1 == p->ny) out += ah * FY[0][(long)(y1 - y0) * RW + (i - x0)];
+        }
+        *outflow = out;
+    }
 
     for (int q = 0; q < 4; ++q) { free(FX[q]); free(FY[q]); }
     free(e.H); free(e.b); free(e.u); free(e.v); free(e.n); free(e.wet);
@@ -490,7 +525,7 @@ double orc_hydro_integral(int nk, const double *tk, const double *Qk, double ta,
  * Returns the count of bad cells (0 = success). */
 long orc_step(const orc_params *p, const double *H, const double *Hu, const double *Hv,
               const double *b, const double *nman, const uint8_t *src, const double *qb,
-              int nk, const double *tk, const double *Qk, double t, double t_end,
+              const double *rain, int nk, const double *tk, const double *Qk, double t, double t_end,
               double *Ho, double *Huo, double *Hvo, double *bo, orc_stepinfo *info)
 {
     orc_dtterms terms;
@@ -509,22 +544,24 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
     int tx = p->tile_x > 0 ? p->tile_x : 64, ty = p->tile_y > 0 ? p->tile_y : 64;
     int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int *cen = NULL;
-    if (p->hgs_skip) {
+    const int skip = p->hgs_skip && !rain;   /* rain wets dry tiles: no skipping */
+    if (skip) {
         orc_params q = *p;
         q.tile_x = tx; q.tile_y = ty;
         cen = (int *)calloc((size_t)ntx * nty, sizeof(int));
         orc_census(&q, H, src, cen);
     }
     long bad = 0, neg = 0, active = 0;
+    double outflow = 0.0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad, neg, active) collapse(2)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad, neg, active, outflow) collapse(2)
 #endif
     for (int by = 0; by < nty; ++by)
         for (int bx = 0; bx < ntx; ++bx) {
             int x0 = bx * tx, y0 = by * ty;
             int x1 = x0 + tx < p->nx ? x0 + tx : p->nx, y1 = y0 + ty < p->ny ? y0 + ty : p->ny;
             int act = 1;
-            if (p->hgs_skip) {
+            if (skip) {
                 int l = bx > 0 ? bx - 1 : bx, r = bx < ntx - 1 ? bx + 1 : bx;
                 int s = by > 0 ? by - 1 : by, nn = by < nty - 1 ? by + 1 : by;
                 act = cen[by * ntx + bx] > 0 || cen[by * ntx + l] > 0 || cen[by * ntx + r] > 0
@@ -532,9 +569,11 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
             }
             if (act) {
                 long ng = 0;
-                bad += orc_step_rect(p, H, Hu, Hv, b, nman, src, qb, dHs, dt, x0, y0, x1, y1,
-                                     Ho, Huo, Hvo, bo, &ng);
+                double of = 0.0;
+                bad += orc_step_rect(p, H, Hu, Hv, b, nman, src, qb, rain, dHs, dt, x0, y0, x1, y1,
+                                     Ho, Huo, Hvo, bo, &ng, &of);
                 neg += ng;
+                outflow += of;
                 ++active;
             } else {
                 for (int j = y0; j < y1; ++j)
@@ -546,7 +585,11 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
         }
     free(cen);
     if (info) {
+        double rv = 0.0;
+        if (rain) for (long k = 0; k < N; ++k) rv += rain[k];
         info->dt = dt; info->binding = binding; info->inflow_vol = vol;
+        info->rain_vol = rv * dt * (p->dx * p->dx);
+        info->outflow_vol = outflow;
         info->n_negative = neg; info->n_bad = bad; info->active_tiles = active;
     }
     return bad;

@@ -366,3 +366,89 @@ def test_hgs_skip_does_not_change_results(orc):
     for x, y in zip(a.arrays(), b.arrays()):
         assert np.array_equal(x, y)
     assert min(i.active_tiles for i in ia) < 96 * 96 // (16 * 8)   # something was skipped
+
+
+# ------------------------------------------- open boundaries and rain (widening)
+
+@pytest.mark.parametrize("u", [2.0, 5.0], ids=["subcritical", "supercritical"])
+def test_open_boundaries_keep_uniform_flow(orc, u):
+    """A uniform flow on a flat frictionless bed has no gradients; with open
+    (zero-gradient) boundaries on all four sides its ghost cells equal the
+    interior, so it must stay uniform to roundoff (with walls it cannot)."""
+    ny, nx = 12, 20
+    H = np.full((ny, nx), 1.0)
+    st0 = _state(orc, H, Hu=u * H, Hv=0.5 * H)
+    p = orc.Params(nx=nx, ny=ny, dx=1.0, bc_w=1, bc_e=1, bc_s=1, bc_n=1)
+    st, _, _ = orc.run(p, st0, 0.0, 40)
+    for a, a0 in zip(st.arrays(), st0.arrays()):
+        assert np.abs(a - a0).max() < 1e-12
+    pw = orc.Params(nx=nx, ny=ny, dx=1.0)
+    sw, _, _ = orc.run(pw, st0, 0.0, 40)
+    assert np.abs(sw.H - 1.0).max() > 1e-3
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (0, 1, 1, 0)], ids=["all_open", "mixed"])
+def test_open_boundary_volume_budget(orc, bc):
+    """Water volume plus the water that left through open sides is constant
+    to roundoff (the boundary fluxes are the update's own fluxes), water does
+    leave, and wall sides pass none."""
+    ny, nx = 40, 48
+    g = I.rng(61)
+    y, x = np.mgrid[0:ny, 0:nx] + 0.5
+    b = g.uniform(-0.02, 0.02, (ny, nx))
+    H = 1.0 + 0.6 * np.exp(-((x - 30) ** 2 + (y - 14) ** 2) / 40.0) - b
+    p = orc.Params(nx=nx, ny=ny, dx=2.0, bc_w=bc[0], bc_e=bc[1], bc_s=bc[2], bc_n=bc[3], tile_x=16, tile_y=16)
+    st = _state(orc, H, b=b)
+    v0 = st.H.sum() * p.dx ** 2
+    out = 0.0
+    for _ in range(150):
+        st, info = orc.step(p, st, 0.02)
+        out += info.outflow_vol
+    v1 = st.H.sum() * p.dx ** 2
+    assert out > 1e-3 * v0
+    assert abs(v0 - v1 - out) < 1e-12 * v0
+
+
+def test_open_boundary_lets_a_dry_bed_dam_break_flow_out(orc):
+    """Ritter's dry-bed dam break on a domain that ends 32 m past the dam:
+    the flow there is supercritical (u - c = (x - x0)/t > 0), so the exact
+    solution is unaffected by what lies beyond, and an open boundary must
+    reproduce it after the front has left (t = 8 s: 0.27 m of water crossing
+    the end, the rarefaction head still 29 m from the left wall); a wall
+    reflects the flow as a bore and cannot."""
+    N, L, x0 = 768, 96.0, 64.0
+    dx = L / N
+    x = (np.arange(N) + 0.5) * dx
+    H = np.where(x < x0, 2.0, 0.0) * np.ones((4, 1))
+    errs = {}
+    for name, bce in (("open", 1), ("wall", 0)):
+        p = orc.Params(nx=N, ny=4, dx=dx, sediment_on=0, bc_e=bce, tile_x=256, tile_y=4)
+        st, t, _ = orc.run(p, _state(orc, H), 0.0, 100000, t_end=8.0)
+        he = _stoker(x, t, 2.0, 0.0, x0)
+        errs[name] = np.abs(st.H[0] - he).sum() / np.abs(he).sum()
+    assert errs["open"] < 0.01, errs
+    assert errs["wall"] > 5 * errs["open"], errs
+
+
+@pytest.mark.parametrize("sigma", [2e-3, -1e-3], ids=["rain", "evaporation"])
+def test_rain_raises_a_lake_uniformly(orc, sigma):
+    """A uniform source sigma (m/s) on a lake at rest over a noisy bed in a
+    closed basin: the free surface stays flat and at rest, and the volume
+    changes by exactly sigma x area x elapsed time."""
+    ny, nx = 24, 32
+    g = I.rng(62)
+    b = g.uniform(-0.05, 0.05, (ny, nx))
+    H = 1.5 - b
+    p = orc.Params(nx=nx, ny=ny, dx=1.0)
+    st = _state(orc, H, b=b)
+    v0 = st.H.sum()
+    rv, t = 0.0, 0.0
+    for _ in range(30):
+        st, info = orc.step(p, st, 0.03, rain=np.full((ny, nx), sigma))
+        rv += info.rain_vol
+        t += info.dt
+    eta = st.H + st.b
+    assert eta.max() - eta.min() < 1e-12
+    assert np.abs(st.Hu).max() < 1e-12 and np.abs(st.Hv).max() < 1e-12
+    assert rv == pytest.approx(sigma * nx * ny * t, rel=1e-12)
+    assert st.H.sum() - v0 == pytest.approx(rv, rel=1e-10)
