@@ -73,7 +73,13 @@ typedef struct {
     int tile_rows;       /* rows per block strip, a multiple of 8; 0 = chosen by the library */
     int block_cols;      /* threads (columns) per block, 128 or 256; 0 = auto */
     double neg_tol;      /* H' < -neg_tol => SWE_ENUMERIC; default 1e-10 (FP64), 1e-4 (FP32) */
+    int bc[4];           /* boundary of the W (x = 0), E, S (y = 0), N sides: SWE_BC_WALL (default,
+                            reflective: the even extension, normal momentum negated) or SWE_BC_OPEN
+                            (zero-gradient outflow: the boundary cell repeated; the paper names no
+                            outflow condition, so this is a reading) */
 } swe_params;
+
+enum { SWE_BC_WALL = 0, SWE_BC_OPEN = 1 };
 
 /* Diagnostics of the current state (swe_get_diag). Volumes are FP64 sums
  * times h^2 over all cells. */
@@ -123,6 +129,11 @@ swe_status swe_set_sources(swe_handle *h, const uint8_t *mask, const double *t,
 /* Bed source q_b^+ - q_b^- of Eq. 1 per cell (nx*ny values, m/s of bed
  * material per unit area); NULL removes it.  Default: none. */
 swe_status swe_set_bed_source(swe_handle *h, const double *q);
+
+/* Per-cell water source sigma of Eq. 6 row 1 in m/s (rain > 0, evaporation
+ * < 0), host array [ny][nx] (copied); H' gains dt sigma each step.  NULL
+ * removes it.  While set, dry blocks are not skipped (rain wets them). */
+swe_status swe_set_rain(swe_handle *h, const double *sigma);
 
 /* Sets the state (H, Hu, Hv, b) from host FP64 arrays of nx*ny values and
  * resets t to 0.  Dry cells (H <= eps_wet) are given zero momentum. */

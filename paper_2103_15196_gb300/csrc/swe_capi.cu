@@ -144,6 +144,8 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
         (p.aj_mode != 0 && p.aj_mode != 1) || p.tile_rows < 0 || (p.tile_rows % 8) != 0 ||
         (p.block_cols != 0 && p.block_cols != 128 && p.block_cols != 256))
         return SWE_EINVAL;
+    for (int q = 0; q < 4; ++q)
+        if (p.bc[q] != SWE_BC_WALL && p.bc[q] != SWE_BC_OPEN) return SWE_EINVAL;
     swe_handle *h = new swe_handle();
     h->p = p;
     if (!(h->p.neg_tol >= 0)) h->p.neg_tol = p.precision == SWE_FP32 ? 1e-4 : 1e-10;
@@ -170,7 +172,8 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     c.m_is_2 = p.m_exp == 2.0 ? 1 : 0;
     c.hgs = p.hgs_skip ? 1 : 0;
     c.literal_D = p.dt_literal_D ? 1 : 0;
-    c.nk = 0; c.has_qb = 0; c.nsrc = 0;
+    c.nk = 0; c.has_qb = 0; c.nsrc = 0; c.has_rain = 0;
+    for (int q = 0; q < 4; ++q) c.bc[q] = p.bc[q];
     c.g = p.g; c.dx = p.dx; c.eps = p.eps_wet;
     c.coef = p.g / (2.0 * p.dx);
     c.cjh = (0.5 * p.C_J) / p.dx;
@@ -329,10 +332,32 @@ extern "C" swe_status swe_set_bed_source(swe_handle *h, const double *q) {
         CU(h, cudaMemcpy(p, a.data(), a.size(), cudaMemcpyHostToDevice));
         h->b.qb = p;
         h->c.has_qb = 1;
-        h->c.hgs = 0;  // a bed source changes dry blocks too
-    } else {
-        h->c.hgs = h->p.hgs_skip ? 1 : 0;
     }
+    // a bed source or rain changes dry blocks too: no skipping while either is set
+    h->c.hgs = (h->p.hgs_skip && !h->c.has_qb && !h->c.has_rain) ? 1 : 0;
+    drop_graphs(h);
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_set_rain(swe_handle *h, const double *sigma) {
+    if (!h) return SWE_EINVAL;
+    CU(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, (void *)h->b.rain);
+    h->b.rain = nullptr;
+    h->c.has_rain = 0;
+    if (sigma) {
+        size_t N = (size_t)h->c.nx * h->c.ny;
+        std::vector<double> v(sigma, sigma + N);
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(h, SWE_EINVAL, "swe_set_rain: non-finite source");
+        std::vector<unsigned char> a = is_f32(h) ? pack<float>(v) : pack<double>(v);
+        void *p = nullptr;
+        CU(h, dev_alloc(h, &p, a.size()));
+        CU(h, cudaMemcpy(p, a.data(), a.size(), cudaMemcpyHostToDevice));
+        h->b.rain = p;
+        h->c.has_rain = 1;
+    }
+    h->c.hgs = (h->p.hgs_skip && !h->c.has_qb && !h->c.has_rain) ? 1 : 0;
     drop_graphs(h);
     return SWE_OK;
 }

@@ -122,13 +122,26 @@ __device__ inline bool is_wet(float H, const SweConst &c) { return H > c.eps_f; 
 __device__ inline bool is_wet(double H, const SweConst &c) { return H > c.eps; }
 
 // Even extension of index i onto [0, n); sgn = -1 after an odd number of reflections.
-__device__ inline int ext_index(int i, int n, int &sgn) {
-    int period = 2 * n;
-    int p = i % period;
-    if (p < 0) p += period;
-    if (p < n) { sgn = 1; return p; }
-    sgn = -1;
-    return period - 1 - p;
+// Ghost index of i for the boundaries below 0 (lo_open) and at n (hi_open):
+// a wall mirrors (the normal momentum's sign flips on every reflection), an
+// open side repeats its boundary cell.  Walls on both sides give the
+// 2n-periodic even extension.  (The loop ends within a few turns for the
+// stencil's reach; the bound only guards it.)
+__device__ inline int ext_index(int i, int n, int lo_open, int hi_open, int &sgn) {
+    int s = 1;
+    for (int it = 0; it < 64; ++it) {
+        if (i < 0) {
+            if (lo_open) { i = 0; break; }
+            i = -1 - i; s = -s;
+        } else if (i >= n) {
+            if (hi_open) { i = n - 1; break; }
+            i = 2 * n - 1 - i; s = -s;
+        } else {
+            break;
+        }
+    }
+    sgn = s;
+    return i;
 }
 
 template <typename T> struct K {  // step constants in the state precision
@@ -278,14 +291,9 @@ template <> __device__ inline K<float> load_k<float>(const SweConst &c, const Sw
 
 // Fast even extension for row indices within one reflection of the grid;
 // falls back to the general form for grids thinner than the stencil.
-__device__ inline int reflect(int i, int n, int &sgn) {
-    if (i >= -n && i < 2 * n) {
-        sgn = 1;
-        if (i < 0) { i = -1 - i; sgn = -1; }
-        else if (i >= n) { i = 2 * n - 1 - i; sgn = -1; }
-        return i;
-    }
-    return ext_index(i, n, sgn);
+__device__ inline int reflect(int i, int n, int lo_open, int hi_open, int &sgn) {
+    if (i >= 0 && i < n) { sgn = 1; return i; }
+    return ext_index(i, n, lo_open, hi_open, sgn);
 }
 
 // Precision-specific arithmetic.  FP32 (production): hardware reciprocal,
@@ -470,7 +478,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             const T syT = T(asy);
             aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
             if (s + 2 <= y1 + 3) {
-                const int yy = reflect(s + 2, c.ny, bsy);
+                const int yy = reflect(s + 2, c.ny, c.bc[2], c.bc[3], bsy);
                 load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
             const bool wet = is_wet(H, c);
@@ -495,7 +503,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             if (wet) {
                 const T bc = Br<P, 2>()[o], u = S.u[PM2_4][o], v = S.v[PM2_4][o];
                 int sy;
-                const int my = reflect(r, c.ny, sy) >> c.man_shift;
+                const int my = reflect(r, c.ny, c.bc[2], c.bc[3], sy) >> c.man_shift;
                 if (my != gn2_row) {
                     gn2_row = my;
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
@@ -540,6 +548,7 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
             T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
+            if (c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
             T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
@@ -660,7 +669,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
     w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
-    w.xx = ext_index(w.x, c.nx, sx);
+    w.xx = reflect(w.x, c.nx, c.bc[0], c.bc[1], sx);
     w.sxT = T(sx);
     w.mcol = w.xx >> c.man_shift;
     w.out_lane = (t >= 4) && (t < BW - 4) && (w.x < c.nx);
@@ -673,9 +682,9 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); }
     w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
-        int yy = reflect(y0 - 4, c.ny, w.asy);
+        int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
         w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
-        yy = reflect(y0 - 3, c.ny, w.bsy);
+        yy = reflect(y0 - 3, c.ny, c.bc[2], c.bc[3], w.bsy);
         w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
     // sweep positions y0-8 .. y1+4 in groups of 4 (y0 is a multiple of 8)

@@ -39,7 +39,22 @@ class Params(ctypes.Structure):
         ("d50", ctypes.c_double), ("s_rel", ctypes.c_double), ("C_Sh", ctypes.c_double),
         ("dt_literal_D", ctypes.c_int), ("precision", ctypes.c_int), ("hgs_skip", ctypes.c_int),
         ("tile_rows", ctypes.c_int), ("block_cols", ctypes.c_int), ("neg_tol", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
     ]
+
+
+_BC_SIDES = {"bc_w": 0, "bc_e": 1, "bc_s": 2, "bc_n": 3}
+SWE_BC_WALL, SWE_BC_OPEN = 0, 1
+
+
+def _set_param(p, key, value):
+    """A swe_params field, or one side's boundary kind (bc_w, bc_e, bc_s, bc_n)."""
+    if key in _BC_SIDES:
+        p.bc[_BC_SIDES[key]] = int(value)
+    elif hasattr(p, key):
+        setattr(p, key, value)
+    else:
+        raise TypeError(f"unknown parameter {key}")
 
 
 class Diag(ctypes.Structure):
@@ -100,6 +115,7 @@ def load_library(build_if_missing: bool = True):
         "swe_set_manning": [H, dp, ctypes.c_int],
         "swe_set_sources": [H, ctypes.POINTER(ctypes.c_uint8), dp, dp, ctypes.c_int],
         "swe_set_bed_source": [H, dp],
+        "swe_set_rain": [H, dp],
         "swe_set_state": [H, dp, dp, dp, dp],
         "swe_set_state_ex": [H, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int],
         "swe_get_state": [H, dp, dp, dp, dp],
@@ -184,9 +200,7 @@ class Solver:
         self._check(L.swe_params_default(ctypes.byref(p), nx, ny, dx), None)
         p.precision = SWE_FP32 if precision == "fp32" else SWE_FP64
         for k, v in kw.items():
-            if not hasattr(p, k):
-                raise TypeError(f"unknown parameter {k}")
-            setattr(p, k, v)
+            _set_param(p, k, v)
         self.params = p
         self.nx, self.ny, self.dx = nx, ny, dx
         self.precision = precision
@@ -228,6 +242,14 @@ class Solver:
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         self._check(self._L.swe_set_sources(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                             _ptr(t), _ptr(Q), len(t)))
+
+    def set_rain(self, sigma):
+        """Per-cell water source in m/s ([ny, nx] or scalar), None to remove."""
+        if sigma is None:
+            self._check(self._L.swe_set_rain(self._h, None))
+        else:
+            s = np.ascontiguousarray(np.broadcast_to(sigma, (self.ny, self.nx)), dtype=np.float64)
+            self._check(self._L.swe_set_rain(self._h, _ptr(s)))
 
     def set_bed_source(self, q):
         if q is None:
@@ -339,7 +361,7 @@ class Ensemble:
             for key, v in sp.items():
                 if key in ("nx", "ny", "dx"):
                     continue
-                setattr(p, key, v)
+                _set_param(p, key, v)
         h = ctypes.c_void_p()
         st = L.swe_ensemble_create(n, arr, ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
         if st != SWE_OK:

@@ -54,10 +54,13 @@ def _fp64_solver(gpu, sc, bw=128, th=32, **kw):
     return S
 
 
-def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, qb=None, **kw):
+def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, qb=None, rain=None,
+                     **kw):
     S = _fp64_solver(gpu, sc, bw=bw, th=th, **kw)
     if qb is not None:
         S.set_bed_source(qb)
+    if rain is not None:
+        S.set_rain(rain)
     d = S.diag()
     p = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, tile_x=d["tile_x"], tile_y=d["tile_y"], **kw)
     n_cell = sc.manning_per_cell()
@@ -66,7 +69,7 @@ def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_censu
     t = 0.0
     worst = np.zeros(4)
     for it in range(nsteps):
-        o, info = orc.step(p, st, n_cell, src=sc.src, qb=qb, hydro=hydro, t=t)
+        o, info = orc.step(p, st, n_cell, src=sc.src, qb=qb, hydro=hydro, t=t, rain=rain)
         dt = S.step()
         g = S.get_state()
         assert dt == pytest.approx(info.dt, rel=1e-13, abs=0), it
@@ -135,45 +138,58 @@ def _moving_sediment_case(side=96, seed=41):
     {"dt_literal_D": 1, "A_J": 0.05},
     {"hgs_skip": 0, "A_J": 0.02},
     {"bed_source": True},
-], ids=["exner_off", "aj_from_eq4", "literal_D", "hgs_off", "bed_source"])
+    {"bc_w": 1, "bc_e": 1, "bc_s": 1, "bc_n": 1},
+    {"bc_e": 1, "bc_n": 1, "A_J": 0.02},
+    {"rain": True},
+], ids=["exner_off", "aj_from_eq4", "literal_D", "hgs_off", "bed_source", "open_all", "open_mixed", "rain"])
 def test_fp64_parity_options(gpu, orc, opts):
     """The step's options against the oracle, per step: the Exner coupling
     off (the surrogate's water-only steps), A_J from Eq. 4, the printed Eq. 7
     D term, HGS skipping off, and a bed source field, with per-cell Manning
-    and an inflow hydrograph on partially wet terrain."""
+    and an inflow hydrograph on partially wet terrain; open (zero-gradient)
+    boundaries on all or some sides; a per-cell rain field."""
     sc = _moving_sediment_case()
-    kw = {k: v for k, v in opts.items() if k != "bed_source"}
-    qb = None
+    kw = {k: v for k, v in opts.items() if k not in ("bed_source", "rain")}
+    qb = rain = None
     if opts.get("bed_source"):
         g = I.rng(43)
         qb = g.normal(0.0, 1e-4, (sc.ny, sc.nx))
+    if opts.get("rain"):
+        g = I.rng(44)
+        rain = g.uniform(0.0, 2e-4, (sc.ny, sc.nx))
     p0 = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, **kw)
     st, t, _ = orc.run(p0, orc.State(sc.H, sc.Hu, sc.Hv, sc.b), sc.manning_per_cell(), 40, src=sc.src,
-                       qb=qb, hydro=orc.Hydrograph(sc.hydro_t, sc.hydro_Q))
+                       qb=qb, hydro=orc.Hydrograph(sc.hydro_t, sc.hydro_Q), rain=rain)
     sc.H, sc.Hu, sc.Hv, sc.b = st.H, st.Hu, st.Hv, st.b
-    worst = _per_step_parity(gpu, orc, sc, 30, bw=128, th=16, qb=qb, **kw)
+    worst = _per_step_parity(gpu, orc, sc, 30, bw=128, th=16, qb=qb, rain=rain, **kw)
     print("fp64 options", opts, "worst rel Linf:", worst)
 
 
-def test_fp32_ragged_multi_tile_per_step(gpu, orc):
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)], ids=["walls", "open"])
+def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc):
     """FP32 state, element by element against the FP64 oracle one step at a
     time from the same inputs, on a 333 x 271 grid (2 x 9 blocks of 248 x 32
-    with ragged right and bottom edges): the per-step FP32 bound of the
-    full-size test (4e-5 m on H and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta)."""
+    with ragged right and bottom edges), walls or open sides: the per-step
+    FP32 bound of the full-size test (4e-5 m on H and b, 4e-5 m^2/s +
+    2e-5 |Hu| on momenta)."""
     nx, ny = 333, 271
     side = max(nx, ny)
     base = I.ensemble_scenario(side, seed=48, manning=0.035, peak=300.0, d50_scale=1.0)
-    H, Hu, Hv, b = (a[:ny, :nx].astype(np.float64) for a in (base.H, base.Hu, base.Hv, base.b))
-    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32)
+    H, b = base.H[:ny, :nx].astype(np.float64), base.b[:ny, :nx].astype(np.float64)
+    Hu, Hv = 0.5 * H, -0.3 * H          # a drift across every side, so the boundaries matter
+    sides = dict(bc_w=bc[0], bc_e=bc[1], bc_s=bc[2], bc_n=bc[3])
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32, **sides)
     S.set_manning(np.full((ny, nx), 0.035), block=0)
     S.set_state(H, Hu, Hv, b)
-    p = orc.Params(nx=nx, ny=ny, dx=base.dx)
+    p = orc.Params(nx=nx, ny=ny, dx=base.dx, **sides)
     ncell = np.full((ny, nx), 0.035)
     worst = np.zeros(4)
+    outflow = 0.0
     for it in range(25):
         st = orc.State(*S.get_state(np.float32))
         st = orc.State(*(a.astype(np.float64) for a in st.arrays()))
         o, info = orc.step(p, st, ncell)
+        outflow += info.outflow_vol
         dt = S.step()
         assert dt == pytest.approx(info.dt, rel=1e-5), it
         got = S.get_state(np.float32)
@@ -183,7 +199,25 @@ def test_fp32_ragged_multi_tile_per_step(gpu, orc):
             worst[q] = max(worst[q], e.max())
             assert np.all(e <= tol), (it, q, e.max())
     S.close()
-    print("fp32 ragged per-step worst abs err (H, Hu, Hv, b):", worst)
+    assert (outflow != 0.0) if bc[0] else (outflow == 0.0)   # water crosses open sides (both ways)
+    print("fp32 ragged per-step", bc, "worst abs err (H, Hu, Hv, b):", worst, "outflow m^3:", outflow)
+
+
+@pytest.mark.parametrize("shape", [(1, 9), (9, 1), (3, 5), (130, 3)])
+@pytest.mark.parametrize("bc", [(1, 0, 0, 1), (0, 1, 1, 0), (1, 1, 1, 1)], ids=["open_wn", "open_es", "open_all"])
+def test_fp64_parity_tiny_grids_open_boundaries(gpu, orc, shape, bc):
+    """Grids narrower than the stencil with open and wall sides mixed: the
+    ghost rule (mirror at walls, repeat at open sides, composed across both
+    ends) must agree with the oracle's."""
+    ny, nx = shape
+    g = I.rng(33)
+    H = 1.0 + g.uniform(0, 0.5, (ny, nx))
+    Hu = g.normal(0, 0.3, (ny, nx))
+    Hv = g.normal(0, 0.3, (ny, nx))
+    b = g.uniform(-0.05, 0.05, (ny, nx))
+    sc = I.Scenario(nx, ny, 1.0, H, Hu, Hv, b, np.full((1, 1), 0.03), manning_block=256)
+    _per_step_parity(gpu, orc, sc, 20, bw=128, th=32, A_J=0.05,
+                     bc_w=bc[0], bc_e=bc[1], bc_s=bc[2], bc_n=bc[3])
 
 
 def test_fp64_advance_lands_on_t_end(gpu, orc):
