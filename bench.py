@@ -173,9 +173,9 @@ def _issue_object(gcell_s, clocks):
             "unit": "Tinst/s", "frac": ach / peak}
 
 
-def make_workload(n, seed=3):
+def make_workload(n, seed=3, wet_fraction=0.5):
     from paper_2103_15196_gb300 import inputs as I
-    return I.half_wet(n, dx=5.0, seed=seed)
+    return I.half_wet(n, dx=5.0, seed=seed, wet_fraction=wet_fraction)
 
 
 def cpu_baseline(sc, budget_s=12.0, win=1024):
@@ -304,6 +304,43 @@ def run_ensemble(args, torch, swe):
             "speedup_vs_sequential": seq_ms / ms,
             "config": "sides 32*U{8..64}, half-wet fractal terrain + channel + inflow hydrograph, "
                       "n~U[0.02,0.06], peak~U[50,1000], d50 scale~U[0.5,2], FP32, seed 4"}
+
+
+def run_hgs_flood(args, torch, swe):
+    """The dry-block skip (K1, Sec. 3) on the kind of scene it is for: the
+    flood-channel terrain at the benchmark's size, initially dry, water
+    entering through the channel head (inflow hydrograph peaking at
+    500 m^3/s).  The same steps with the skip on and off; rates count every
+    cell of the grid per step."""
+    from paper_2103_15196_gb300 import inputs as I
+    n, K, W = args.size, args.hgs_steps, 5
+    sc = I.flood_channel(n, dx=5.0, seed=2, peak=500.0)
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, skip in (("on", 1), ("off", 0)):
+        S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=skip,
+                       tile_rows=args.hgs_tile_rows)
+        S.set_manning(sc.manning, block=sc.manning_block)
+        S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
+        S.set_state(*(np.asarray(a, dtype=np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)))
+        S.run_steps(W)
+        S.sync()
+        d0 = S.diag()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.run_steps(K)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        d1 = S.diag()
+        out[name] = {"value": _aggregate_rate(float(n) * n, K, ms * 1e-3, 1), "ms_per_step": ms / K,
+                     "active_cell_fraction": (d1["cells_computed"] - d0["cells_computed"]) / (float(n) * n * K),
+                     "wet_cells_end": d1["wet_cells"], "t_end": d1["t"]}
+        S.close()
+    return {"workload": f"flood channel {n}x{n}, initially dry, inflow on the channel head, steps {W}..{W + K}",
+            "tile_rows": args.hgs_tile_rows,
+            "unit": UNIT, "skip_on": out["on"], "skip_off": out["off"],
+            "speedup": out["on"]["value"] / out["off"]["value"]}
 
 
 def run_surrogate(args, torch, swe):
@@ -499,7 +536,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     n, K, W = args.size, args.steps, args.warmup
-    sc = make_workload(n)
+    sc = make_workload(n, wet_fraction=args.wet_fraction)
     stream = torch.cuda.Stream()
     S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=0 if args.hgs_off else 1,
                    tile_rows=args.tile_rows, block_cols=args.block_cols)
@@ -560,6 +597,9 @@ def run_ours(args):
     ens = None
     if world == 1 and not args.no_ensemble:
         ens = run_ensemble(args, torch, swe)
+    hgs_flood = None
+    if world == 1 and not args.no_hgs_flood:
+        hgs_flood = run_hgs_flood(args, torch, swe)
     sur = None
     if world == 1 and not args.no_surrogate:
         sur = run_surrogate(args, torch, swe)
@@ -577,7 +617,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"half-wet fractal terrain {n}x{n} ({n * n} cells), dx=5 m, 20 m relief, "
+        "config": {"workload": f"{args.wet_fraction:.0%}-wet fractal terrain {n}x{n} ({n * n} cells), dx=5 m, 20 m relief, "
                                f"carved channel, 2 m dam-break step, Manning per 64^2 block, FP32 state, "
                                f"FP64 dt/accumulators, HGS {'off' if args.hgs_off else 'on'}",
                    "grid": n, "l2_flush": "inputs larger than L2 (2 x 4.3 GB ping-pong state)",
@@ -597,6 +637,7 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cb,
         "ensemble": ens,
+        "hgs_flood": hgs_flood,
         "surrogate": sur,
     }
     print(json.dumps(line), flush=True)
@@ -613,6 +654,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=16384)
     ap.add_argument("--hgs-off", action="store_true")
+    ap.add_argument("--wet-fraction", type=float, default=0.5, help="initially wet fraction of the terrain")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per block strip (0: library default)")
     ap.add_argument("--block-cols", type=int, default=0, help="threads per block, 128 or 256 (0: default)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -621,6 +663,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-hgs-flood", action="store_true")
+    ap.add_argument("--hgs-steps", type=int, default=200)
+    ap.add_argument("--hgs-tile-rows", type=int, default=64, help="block strip height of the dry-start flood leg")
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-surrogate", action="store_true")

@@ -189,6 +189,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = dev_alloc(h, &b.buf[q], (size_t)ncell * h->cell_bytes);
     for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = dev_alloc(h, (void **)&b.census[q], ntiles * sizeof(int));
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.skipped, ntiles);
+    if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.work, (ntiles + 2) * sizeof(int));
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.dev, sizeof(SweDev));
     h->diag_blocks = (int)std::min<long long>(1024, (ncell + 255) / 256);
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.partials, sizeof(double) * 3 * h->diag_blocks);
@@ -653,14 +654,15 @@ int handle_retile(swe_handle *h, int bw, int th) {
     const int tw = bw - 8;
     const int tx = (c.nx + tw - 1) / tw, ty = (c.ny + th - 1) / th;
     const size_t nt = (size_t)tx * ty;
-    void *cen0 = nullptr, *cen1 = nullptr, *skp = nullptr;
+    void *cen0 = nullptr, *cen1 = nullptr, *skp = nullptr, *wrk = nullptr;
     if (dev_alloc(h, &cen0, nt * sizeof(int)) != cudaSuccess || dev_alloc(h, &cen1, nt * sizeof(int)) != cudaSuccess ||
-        dev_alloc(h, &skp, nt) != cudaSuccess) {
-        dev_free(h, cen0); dev_free(h, cen1); dev_free(h, skp);
+        dev_alloc(h, &skp, nt) != cudaSuccess || dev_alloc(h, &wrk, (nt + 2) * sizeof(int)) != cudaSuccess) {
+        dev_free(h, cen0); dev_free(h, cen1); dev_free(h, skp); dev_free(h, wrk);
         return SWE_ENOMEM;
     }
-    dev_free(h, h->b.census[0]); dev_free(h, h->b.census[1]); dev_free(h, h->b.skipped);
+    dev_free(h, h->b.census[0]); dev_free(h, h->b.census[1]); dev_free(h, h->b.skipped); dev_free(h, h->b.work);
     h->b.census[0] = (int *)cen0; h->b.census[1] = (int *)cen1; h->b.skipped = (unsigned char *)skp;
+    h->b.work = (int *)wrk;
     h->bw = bw;
     c.tw = tw; c.th = th; c.tiles_x = tx; c.tiles_y = ty;
     drop_graphs(h);

@@ -57,6 +57,7 @@ struct SweBufs {
     void *buf[2];               // AoS state cells {H, Hu, Hv, b}, ping-pong
     int *census[2];             // Index_block of K1 for state^n (census[n & 1])
     unsigned char *skipped;     // per block: 1 = both buffers equal on the block
+    int *work;                  // blocks to run this step: [0] count, [1] unused, [2..] block indices
     const void *gn2;            // g n^2 table (element type = state type)
     const void *ajn;            // 0.05 n^3 table (Eq. 4 numerator)
     const int *src_rowptr;      // ny + 1 offsets into src_x

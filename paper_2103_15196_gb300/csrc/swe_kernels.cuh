@@ -705,12 +705,69 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
 }
 
-// One step: one block per (column band, row strip).
+// The blocks the next step must run (HGS region of K1, Sec. 3, compacted):
+// those active by the K1 rule (the block or one of its four edge neighbours
+// holds water or a source) and dry ones whose two state buffers still
+// differ (one copy carries them over).  Written in block order to work[2..],
+// with the count in work[0] (work[1] is not used).  The
+// census of the next state is 0 for every block left out (it stays dry), so
+// it is written here for them.  Without the dry-block skip every block is
+// listed.  One block of 1024 threads (T: the state type, for one instance
+// per precision's translation unit).
+template <typename T>
+__global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
+    __shared__ int wsum[32];
+    __shared__ int base, chunk;
+    const long long n = B.dev->n;
+    const int *cen = (n & 1) ? B.census[1] : B.census[0];
+    int *cen_next = (n & 1) ? B.census[0] : B.census[1];
+    const int nt = c.tiles_x * c.tiles_y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < nt; t0 += 1024) {
+        const int tile = t0 + (int)threadIdx.x;
+        bool need = false;
+        if (tile < nt) {
+            need = true;
+            if (c.hgs) {
+                const int bx = tile % c.tiles_x, by = tile / c.tiles_x;
+                const int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
+                const int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
+                const bool active = cen[tile] > 0 || cen[by * c.tiles_x + l] > 0 || cen[by * c.tiles_x + r] > 0 ||
+                                    cen[d * c.tiles_x + bx] > 0 || cen[u * c.tiles_x + bx] > 0;
+                need = active || !B.skipped[tile];
+                if (!need) cen_next[tile] = 0;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {   // exclusive prefix over the warps, and the chunk's total
+            int acc = 0;
+            for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
+            chunk = acc;
+        }
+        __syncthreads();
+        if (need) B.work[2 + base + wsum[w] + __popc(m & ((1u << lane) - 1u))] = tile;
+        __syncthreads();
+        if (threadIdx.x == 0) base += chunk;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) B.work[0] = base;
+}
+
+// One step: one CUDA block per grid block; CUDA block i runs entry i of the
+// work list (a column band x row strip), blocks past the list's end return at
+// once.  With every block listed this is one block per grid block in order.
 template <typename T, int BW>
 __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
-    step_tile<T, BW, false>(c, B, blockIdx.x, blockIdx.y, S);
+    const int i = blockIdx.x;
+    if (i >= B.work[0]) return;
+    const int tile = B.work[2 + i];
+    step_tile<T, BW, false>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state

@@ -9,6 +9,8 @@ template <typename T> size_t step_smem_bytes(int bw) {
     return bw == 128 ? sizeof(StepSmem<T, 128>) : sizeof(StepSmem<T, 256>);
 }
 
+// One step: the work list of the blocks to run (compact_kernel), then one
+// CUDA block per grid block, the unlisted ones returning at once.
 template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
     static bool configured = false;
     const size_t smem = sizeof(StepSmem<T, BW>);
@@ -17,8 +19,8 @@ template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid(c.tiles_x, c.tiles_y);
-    step_kernel<T, BW><<<grid, BW, smem, s>>>(c, b);
+    compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
+    step_kernel<T, BW><<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
     return cudaGetLastError();
 }
 

@@ -117,7 +117,8 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     const size_t off_cen0 = align256(off_dev + sizeof(SweDev));
     const size_t off_cen1 = align256(off_cen0 + ntiles * sizeof(int));
     const size_t off_skip = align256(off_cen1 + ntiles * sizeof(int));
-    const size_t off_rows = align256(off_skip + ntiles);
+    const size_t off_work = align256(off_skip + ntiles);
+    const size_t off_rows = align256(off_work + (ntiles + 2) * sizeof(int));
     const size_t off_gn2 = align256(off_rows + ((size_t)p.ny + 1) * sizeof(int));
     const size_t off_ajn = off_gn2 + 128;
     const size_t total = off_ajn + 128;
@@ -133,6 +134,7 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     b.census[0] = (int *)(base + off_cen0);
     b.census[1] = (int *)(base + off_cen1);
     b.skipped = base + off_skip;
+    b.work = (int *)(base + off_work);
     b.src_rowptr = (const int *)(base + off_rows);
     b.src_x = nullptr;
     b.hyd_t = nullptr; b.hyd_q = nullptr; b.qb = nullptr;
