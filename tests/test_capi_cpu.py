@@ -35,3 +35,18 @@ def test_create_rejects_bad_params_before_touching_the_device():
         q = swe.Params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert L.swe_create(ctypes.byref(q), None, ctypes.byref(h)) == swe.SWE_EINVAL, field
+    for side in range(4):
+        q = swe.Params.from_buffer_copy(p)
+        q.bc[side] = 2                      # neither a wall nor an open side
+        assert L.swe_create(ctypes.byref(q), None, ctypes.byref(h)) == swe.SWE_EINVAL, side
+
+
+def test_boundary_kinds_default_to_walls_and_map_by_side():
+    L = swe.load_library()
+    p = swe.Params()
+    L.swe_params_default(ctypes.byref(p), 8, 8, 1.0)
+    assert list(p.bc) == [swe.SWE_BC_WALL] * 4
+    for k, side in enumerate(("bc_w", "bc_e", "bc_s", "bc_n")):
+        q = swe.Params.from_buffer_copy(p)
+        swe._set_param(q, side, swe.SWE_BC_OPEN)
+        assert [q.bc[i] for i in range(4)] == [int(i == k) for i in range(4)]
