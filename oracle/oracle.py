@@ -57,6 +57,7 @@ class _DtTerms(ctypes.Structure):
 class _StepInfo(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("binding", ctypes.c_int),
                 ("inflow_vol", ctypes.c_double), ("rain_vol", ctypes.c_double), ("outflow_vol", ctypes.c_double),
+                ("infil_vol", ctypes.c_double),
                 ("n_negative", ctypes.c_long), ("n_bad", ctypes.c_long), ("active_tiles", ctypes.c_long)]
 
 
@@ -106,14 +107,14 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         u8 = ctypes.POINTER(ctypes.c_uint8)
         L.orc_step.restype = ctypes.c_long
-        L.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp,
+        L.orc_step.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp, dp,
                                ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                dp, dp, dp, dp, ctypes.POINTER(_StepInfo)]
         L.orc_step_rect.restype = ctypes.c_long
-        L.orc_step_rect.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp,
+        L.orc_step_rect.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, dp, u8, dp, dp, dp,
                                     ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                    dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long), dp]
+                                    dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long), dp, dp]
         L.orc_dt_terms.restype = ctypes.c_int
         L.orc_dt_terms.argtypes = [ctypes.POINTER(_Params), dp, dp, dp, dp, ctypes.POINTER(_DtTerms)]
         L.orc_dt.restype = ctypes.c_double
@@ -180,6 +181,7 @@ class StepInfo:
     active_tiles: int
     rain_vol: float = 0.0
     outflow_vol: float = 0.0
+    infil_vol: float = 0.0
 
 
 def _prep(p: Params, st: State, n, src, qb):
@@ -199,14 +201,18 @@ def _prep(p: Params, st: State, n, src, qb):
 
 
 def step(p: Params, st: State, n, src=None, qb=None, hydro: Hydrograph | None = None,
-         t: float = 0.0, t_end: float = -1.0, rain=None):
-    """One full step (K1..K8).  rain: per-cell water source in m/s (or None).
+         t: float = 0.0, t_end: float = -1.0, rain=None, beta=None):
+    """One full step (K1..K8).  rain: per-cell water source in m/s; beta:
+    per-cell infiltration rate in m/s (each None or an array/scalar).
     Returns (new State, StepInfo)."""
     H, Hu, Hv, b, n, src, srcp, qb, qbp = _prep(p, st, n, src, qb)
-    rainp = None
+    rainp = betap = None
     if rain is not None:
         rain = _f64(np.broadcast_to(rain, H.shape), H.shape)
         rainp = _d(rain)
+    if beta is not None:
+        beta = _f64(np.broadcast_to(beta, H.shape), H.shape)
+        betap = _d(beta)
     out = [np.empty_like(H) for _ in range(4)]
     info = _StepInfo()
     pc = p.c()
@@ -214,10 +220,10 @@ def step(p: Params, st: State, n, src=None, qb=None, hydro: Hydrograph | None = 
         nk, tk, Qk = len(hydro.t), _d(hydro.t), _d(hydro.Q)
     else:
         nk, tk, Qk = 0, None, None
-    lib().orc_step(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, rainp,
+    lib().orc_step(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, rainp, betap,
                    nk, tk, Qk, t, t_end, *(_d(o) for o in out), ctypes.byref(info))
     return State(*out), StepInfo(info.dt, info.binding, info.inflow_vol, info.n_negative,
-                                 info.n_bad, info.active_tiles, info.rain_vol, info.outflow_vol)
+                                 info.n_bad, info.active_tiles, info.rain_vol, info.outflow_vol, info.infil_vol)
 
 
 def step_rect(p: Params, st: State, n, dt: float, rect, src=None, qb=None, dHs: float = 0.0):
@@ -228,8 +234,8 @@ def step_rect(p: Params, st: State, n, dt: float, rect, src=None, qb=None, dHs: 
     out = [np.zeros_like(H) for _ in range(4)]
     nneg = ctypes.c_long(0)
     pc = p.c()
-    bad = lib().orc_step_rect(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, None,
-                              dHs, dt, x0, y0, x1, y1, *(_d(o) for o in out), ctypes.byref(nneg), None)
+    bad = lib().orc_step_rect(ctypes.byref(pc), _d(H), _d(Hu), _d(Hv), _d(b), _d(n), srcp, qbp, None, None,
+                              dHs, dt, x0, y0, x1, y1, *(_d(o) for o in out), ctypes.byref(nneg), None, None)
     return [o[y0:y1, x0:x1].copy() for o in out], bad
 
 
@@ -269,13 +275,13 @@ def hll(UL, UR, FL, FR, sL, sR):
 
 
 def run(p: Params, st: State, n, nsteps: int, src=None, qb=None, hydro=None, t: float = 0.0,
-        t_end: float = -1.0, on_step=None, rain=None):
+        t_end: float = -1.0, on_step=None, rain=None, beta=None):
     """Advances nsteps (or until t_end).  Returns (State, t, list of StepInfo)."""
     infos = []
     for _ in range(nsteps):
         if t_end > 0 and t >= t_end:
             break
-        st, info = step(p, st, n, src=src, qb=qb, hydro=hydro, t=t, t_end=t_end, rain=rain)
+        st, info = step(p, st, n, src=src, qb=qb, hydro=hydro, t=t, t_end=t_end, rain=rain, beta=beta)
         t = t_end if info.binding == 4 else t + info.dt   # a clipped step lands on t_end
         infos.append(info)
         if on_step is not None:

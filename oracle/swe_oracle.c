@@ -71,6 +71,7 @@ typedef struct {
     double inflow_vol;  /* water volume added by sources during the step */
     double rain_vol;    /* water volume added by the per-cell source (rain) */
     double outflow_vol; /* water volume that left through open boundaries */
+    double infil_vol;   /* water volume lost to infiltration */
     long n_negative;    /* cells with H' < 0 */
     long n_bad;         /* cells with H' < -neg_tol or a non-finite result */
     long active_tiles;  /* tiles computed (HGS) */
@@ -273,15 +274,19 @@ static double *xalloc(long n) { return (double *)calloc((size_t)n, sizeof(double
  * given source depth increment dHs (added to source-flagged cells).  Writes
  * only the rectangle of the full-size output arrays.  qb (nullable) is the
  * per-cell bed source q_b^+ - q_b^- of Eq. 1; rain (nullable) a per-cell
- * water source sigma of Eq. 6 row 1 in m/s (rain > 0, evaporation < 0).
+ * water source sigma of Eq. 6 row 1 in m/s (rain > 0, evaporation < 0);
+ * beta (nullable) the absorption (infiltration) rate of Sec. 3 in m/s >= 0,
+ * a loss capped by the water present that takes its share of momentum
+ * (READING: the paper names beta(x, y) but gives no law).
  * Returns the number of cells with H' < -neg_tol or a non-finite result;
  * *nneg counts H' < 0; *outflow (nullable) gets the volume of water that
  * left the grid through the rectangle's part of the domain boundary. */
 long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
                    const double *Hv, const double *b, const double *nman,
-                   const uint8_t *src, const double *qb, const double *rain, double dHs, double dt,
-                   int x0, int y0, int x1, int y1,
-                   double *Ho, double *Huo, double *Hvo, double *bo, long *nneg, double *outflow)
+                   const uint8_t *src, const double *qb, const double *rain, const double *beta,
+                   double dHs, double dt, int x0, int y0, int x1, int y1,
+                   double *Ho, double *Huo, double *Hvo, double *bo, long *nneg, double *outflow,
+                   double *infil)
 {
     const int R = ORC_R;
     ext_t e;
@@ -448,6 +453,7 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
     double cb = dtdx / (1.0 - p->psi);
     double cq = dt / (1.0 - p->psi);
     long bad = 0, neg = 0;
+    double lost = 0.0;
     for (int j = y0; j < y1; ++j)
         for (int i = x0; i < x1; ++i) {
             long c = E(&e, i, j), k = (long)j * p->nx + i;
@@ -460,6 +466,18 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
                 if (rain) hn = hn + dt * rain[k];
                 hun = e.H[c] * e.wx[c] - dtdx * ((FX[1][fe] - FX[1][fw]) + (FY[1][fn] - FY[1][fs]));
                 hvn = e.H[c] * e.wy[c] - dtdx * ((FX[2][fe] - FX[2][fw]) + (FY[2][fn] - FY[2][fs]));
+                if (beta) {
+                    /* infiltration: at most the water present, with its share of momentum */
+                    double loss = dt * beta[k];
+                    if (loss > hn) loss = hn > 0.0 ? hn : 0.0;
+                    if (loss > 0.0) {
+                        double r = (hn - loss) / hn;
+                        hn = hn - loss;
+                        hun = hun * r;
+                        hvn = hvn * r;
+                        lost += loss;
+                    }
+                }
                 if (!(hn > p->eps_wet)) { hun = 0.0; hvn = 0.0; }
             } else {
                 hn = H[k]; hun = Hu[k]; hvn = Hv[k];
@@ -471,6 +489,7 @@ long orc_step_rect(const orc_params *p, const double *H, const double *Hu,
             if (!(hn >= -p->neg_tol) || !isfinite(hn) || !isfinite(bn) || !isfinite(hun) || !isfinite(hvn)) ++bad;
         }
     if (nneg) *nneg = neg;
+    if (infil) *infil = lost * (p->dx * p->dx);
     if (outflow) {
         /* mass fluxes through the domain's boundary faces (zero at walls) */
         double out = 0.0, ah = dt * p->dx;
@@ -525,7 +544,8 @@ double orc_hydro_integral(int nk, const double *tk, const double *Qk, double ta,
  * Returns the count of bad cells (0 = success). */
 long orc_step(const orc_params *p, const double *H, const double *Hu, const double *Hv,
               const double *b, const double *nman, const uint8_t *src, const double *qb,
-              const double *rain, int nk, const double *tk, const double *Qk, double t, double t_end,
+              const double *rain, const double *beta, int nk, const double *tk, const double *Qk,
+              double t, double t_end,
               double *Ho, double *Huo, double *Hvo, double *bo, orc_stepinfo *info)
 {
     orc_dtterms terms;
@@ -552,9 +572,9 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
         orc_census(&q, H, src, cen);
     }
     long bad = 0, neg = 0, active = 0;
-    double outflow = 0.0;
+    double outflow = 0.0, infil = 0.0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad, neg, active, outflow) collapse(2)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad, neg, active, outflow, infil) collapse(2)
 #endif
     for (int by = 0; by < nty; ++by)
         for (int bx = 0; bx < ntx; ++bx) {
@@ -569,11 +589,12 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
             }
             if (act) {
                 long ng = 0;
-                double of = 0.0;
-                bad += orc_step_rect(p, H, Hu, Hv, b, nman, src, qb, rain, dHs, dt, x0, y0, x1, y1,
-                                     Ho, Huo, Hvo, bo, &ng, &of);
+                double of = 0.0, il = 0.0;
+                bad += orc_step_rect(p, H, Hu, Hv, b, nman, src, qb, rain, beta, dHs, dt, x0, y0, x1, y1,
+                                     Ho, Huo, Hvo, bo, &ng, &of, &il);
                 neg += ng;
                 outflow += of;
+                infil += il;
                 ++active;
             } else {
                 for (int j = y0; j < y1; ++j)
@@ -590,6 +611,7 @@ long orc_step(const orc_params *p, const double *H, const double *Hu, const doub
         info->dt = dt; info->binding = binding; info->inflow_vol = vol;
         info->rain_vol = rv * dt * (p->dx * p->dx);
         info->outflow_vol = outflow;
+        info->infil_vol = infil;
         info->n_negative = neg; info->n_bad = bad; info->active_tiles = active;
     }
     return bad;

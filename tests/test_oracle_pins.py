@@ -452,3 +452,39 @@ def test_rain_raises_a_lake_uniformly(orc, sigma):
     assert np.abs(st.Hu).max() < 1e-12 and np.abs(st.Hv).max() < 1e-12
     assert rv == pytest.approx(sigma * nx * ny * t, rel=1e-12)
     assert st.H.sum() - v0 == pytest.approx(rv, rel=1e-10)
+
+
+def test_infiltration_drains_a_lake_at_its_rate_and_stops_at_zero(orc):
+    """A flat lake at rest, uniform absorption rate beta: the depth falls by
+    exactly beta dt per step while water lasts, never below zero, the lake
+    stays at rest, and the infiltrated volume is what the lake lost."""
+    ny, nx, beta, H0 = 10, 14, 2e-3, 0.05
+    H = np.full((ny, nx), H0)
+    p = orc.Params(nx=nx, ny=ny, dx=1.0, sediment_on=0)
+    st = _state(orc, H)
+    lost, t = 0.0, 0.0
+    for _ in range(400):
+        st, info = orc.step(p, st, 0.03, beta=beta)
+        lost += info.infil_vol
+        t += info.dt
+        assert st.H.min() >= 0.0
+        expect = max(H0 - beta * t, 0.0)
+        assert np.abs(st.H - expect).max() < 1e-12 * max(1.0, t)
+        assert not st.Hu.any() and not st.Hv.any()
+        if expect == 0.0:
+            break
+    assert st.H.max() == 0.0, "the lake must drain completely"
+    assert lost == pytest.approx(H0 * nx * ny, rel=1e-12)
+
+
+def test_infiltration_keeps_the_velocity_of_a_uniform_flow(orc):
+    """Infiltration takes its share of momentum: a uniform flow with open
+    boundaries loses depth uniformly while its velocity stays unchanged."""
+    ny, nx = 8, 12
+    H = np.full((ny, nx), 1.0)
+    p = orc.Params(nx=nx, ny=ny, dx=1.0, bc_w=1, bc_e=1, bc_s=1, bc_n=1)
+    st = _state(orc, H, Hu=1.5 * H, Hv=-0.5 * H)
+    for _ in range(20):
+        st, _ = orc.step(p, st, 0.0, beta=1e-3)
+    assert st.H.max() < 1.0 and np.ptp(st.H) < 1e-13
+    assert np.abs(st.Hu / st.H - 1.5).max() < 1e-12 and np.abs(st.Hv / st.H + 0.5).max() < 1e-12
