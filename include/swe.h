@@ -135,6 +135,13 @@ swe_status swe_set_bed_source(swe_handle *h, const double *q);
  * removes it.  While set, dry blocks are not skipped (rain wets them). */
 swe_status swe_set_rain(swe_handle *h, const double *sigma);
 
+/* Per-cell infiltration (absorption) rate beta >= 0 of Sec. 3 in m/s, host
+ * array [ny][nx] (copied); each step a cell loses min(dt beta, H') of depth
+ * and the same fraction of its momentum (the paper names beta(x, y) but no
+ * law; this is a reading).  NULL removes it.  SWE_EINVAL for a negative or
+ * non-finite rate. */
+swe_status swe_set_infiltration(swe_handle *h, const double *beta);
+
 /* Sets the state (H, Hu, Hv, b) from host FP64 arrays of nx*ny values and
  * resets t to 0.  Dry cells (H <= eps_wet) are given zero momentum. */
 swe_status swe_set_state(swe_handle *h, const double *H, const double *Hu,

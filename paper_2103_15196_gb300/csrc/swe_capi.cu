@@ -172,7 +172,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     c.m_is_2 = p.m_exp == 2.0 ? 1 : 0;
     c.hgs = p.hgs_skip ? 1 : 0;
     c.literal_D = p.dt_literal_D ? 1 : 0;
-    c.nk = 0; c.has_qb = 0; c.nsrc = 0; c.has_rain = 0;
+    c.nk = 0; c.has_qb = 0; c.nsrc = 0; c.has_rain = 0; c.has_beta = 0;
     for (int q = 0; q < 4; ++q) c.bc[q] = p.bc[q];
     c.g = p.g; c.dx = p.dx; c.eps = p.eps_wet;
     c.coef = p.g / (2.0 * p.dx);
@@ -336,6 +336,28 @@ extern "C" swe_status swe_set_bed_source(swe_handle *h, const double *q) {
     }
     // a bed source or rain changes dry blocks too: no skipping while either is set
     h->c.hgs = (h->p.hgs_skip && !h->c.has_qb && !h->c.has_rain) ? 1 : 0;
+    drop_graphs(h);
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_set_infiltration(swe_handle *h, const double *beta) {
+    if (!h) return SWE_EINVAL;
+    CU(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, (void *)h->b.beta);
+    h->b.beta = nullptr;
+    h->c.has_beta = 0;
+    if (beta) {
+        size_t N = (size_t)h->c.nx * h->c.ny;
+        std::vector<double> v(beta, beta + N);
+        for (double x : v)
+            if (!(x >= 0.0) || !std::isfinite(x)) return fail(h, SWE_EINVAL, "swe_set_infiltration: rate must be >= 0");
+        std::vector<unsigned char> a = is_f32(h) ? pack<float>(v) : pack<double>(v);
+        void *p = nullptr;
+        CU(h, dev_alloc(h, &p, a.size()));
+        CU(h, cudaMemcpy(p, a.data(), a.size(), cudaMemcpyHostToDevice));
+        h->b.beta = p;
+        h->c.has_beta = 1;
+    }
     drop_graphs(h);
     return SWE_OK;
 }

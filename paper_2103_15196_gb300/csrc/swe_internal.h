@@ -40,6 +40,7 @@ struct SweConst {
     int nsrc;               // number of source cells
     int bc[4];              // W, E, S, N boundaries: 0 wall (mirror), 1 open (repeat the boundary cell)
     int has_rain;           // per-cell water source present
+    int has_beta;           // per-cell infiltration rate present
     double g, dx, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, C_J, psi, K, dt_max, neg_tol;
     float eps_f;            // largest float <= eps: (float)H > eps_f <=> (double)H > eps
     struct { float g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol; } f;  // the same, rounded to FP32
@@ -65,6 +66,7 @@ struct SweBufs {
     const double *hyd_t, *hyd_q;
     const void *qb;             // optional bed source per cell (state type)
     const void *rain;           // optional water source per cell, m/s (state type)
+    const void *beta;           // optional infiltration rate per cell, m/s (state type)
     SweDev *dev;
     double *partials;           // diagnostics scratch: 3 doubles per block
 };

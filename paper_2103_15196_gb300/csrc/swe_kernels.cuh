@@ -551,6 +551,17 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             if (c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
             T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
+            if (c.has_beta) {
+                // infiltration: at most the water present, with its share of momentum
+                T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
+                if (loss > hn) loss = hn > T(0) ? hn : T(0);
+                if (loss > T(0)) {
+                    const T ratio = (hn - loss) / hn;
+                    hn = hn - loss;
+                    hun = hun * ratio;
+                    hvn = hvn * ratio;
+                }
+            }
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
             const T bn = bc - k.cb * ((S.xf[PM5_2][3][o] - S.xf[PM5_2][3][o - 1]) + (G1[3] - G2[3]));
             CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);

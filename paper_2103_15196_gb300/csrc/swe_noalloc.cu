@@ -99,7 +99,7 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     c.m_is_2 = p.m_exp == 2.0 ? 1 : 0;
     c.hgs = p.hgs_skip ? 1 : 0;
     c.literal_D = p.dt_literal_D ? 1 : 0;
-    c.nk = 0; c.has_qb = 0; c.nsrc = 0; c.has_rain = 0;
+    c.nk = 0; c.has_qb = 0; c.nsrc = 0; c.has_rain = 0; c.has_beta = 0;
     for (int q = 0; q < 4; ++q) c.bc[q] = p.bc[q];
     c.g = p.g; c.dx = p.dx; c.eps = p.eps_wet;
     c.coef = p.g / (2.0 * p.dx);

@@ -116,6 +116,7 @@ def load_library(build_if_missing: bool = True):
         "swe_set_sources": [H, ctypes.POINTER(ctypes.c_uint8), dp, dp, ctypes.c_int],
         "swe_set_bed_source": [H, dp],
         "swe_set_rain": [H, dp],
+        "swe_set_infiltration": [H, dp],
         "swe_set_state": [H, dp, dp, dp, dp],
         "swe_set_state_ex": [H, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int],
         "swe_get_state": [H, dp, dp, dp, dp],
@@ -250,6 +251,14 @@ class Solver:
         else:
             s = np.ascontiguousarray(np.broadcast_to(sigma, (self.ny, self.nx)), dtype=np.float64)
             self._check(self._L.swe_set_rain(self._h, _ptr(s)))
+
+    def set_infiltration(self, beta):
+        """Per-cell infiltration rate in m/s ([ny, nx] or scalar), None to remove."""
+        if beta is None:
+            self._check(self._L.swe_set_infiltration(self._h, None))
+        else:
+            s = np.ascontiguousarray(np.broadcast_to(beta, (self.ny, self.nx)), dtype=np.float64)
+            self._check(self._L.swe_set_infiltration(self._h, _ptr(s)))
 
     def set_bed_source(self, q):
         if q is None:

@@ -55,12 +55,14 @@ def _fp64_solver(gpu, sc, bw=128, th=32, **kw):
 
 
 def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_census=True, qb=None, rain=None,
-                     **kw):
+                     beta=None, **kw):
     S = _fp64_solver(gpu, sc, bw=bw, th=th, **kw)
     if qb is not None:
         S.set_bed_source(qb)
     if rain is not None:
         S.set_rain(rain)
+    if beta is not None:
+        S.set_infiltration(beta)
     d = S.diag()
     p = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, tile_x=d["tile_x"], tile_y=d["tile_y"], **kw)
     n_cell = sc.manning_per_cell()
@@ -69,7 +71,7 @@ def _per_step_parity(gpu, orc, sc, nsteps, bw=128, th=32, tol=1e-11, check_censu
     t = 0.0
     worst = np.zeros(4)
     for it in range(nsteps):
-        o, info = orc.step(p, st, n_cell, src=sc.src, qb=qb, hydro=hydro, t=t, rain=rain)
+        o, info = orc.step(p, st, n_cell, src=sc.src, qb=qb, hydro=hydro, t=t, rain=rain, beta=beta)
         dt = S.step()
         g = S.get_state()
         assert dt == pytest.approx(info.dt, rel=1e-13, abs=0), it
@@ -141,7 +143,9 @@ def _moving_sediment_case(side=96, seed=41):
     {"bc_w": 1, "bc_e": 1, "bc_s": 1, "bc_n": 1},
     {"bc_e": 1, "bc_n": 1, "A_J": 0.02},
     {"rain": True},
-], ids=["exner_off", "aj_from_eq4", "literal_D", "hgs_off", "bed_source", "open_all", "open_mixed", "rain"])
+    {"infiltration": True},
+], ids=["exner_off", "aj_from_eq4", "literal_D", "hgs_off", "bed_source", "open_all", "open_mixed", "rain",
+        "infiltration"])
 def test_fp64_parity_options(gpu, orc, opts):
     """The step's options against the oracle, per step: the Exner coupling
     off (the surrogate's water-only steps), A_J from Eq. 4, the printed Eq. 7
@@ -149,19 +153,22 @@ def test_fp64_parity_options(gpu, orc, opts):
     and an inflow hydrograph on partially wet terrain; open (zero-gradient)
     boundaries on all or some sides; a per-cell rain field."""
     sc = _moving_sediment_case()
-    kw = {k: v for k, v in opts.items() if k not in ("bed_source", "rain")}
-    qb = rain = None
+    kw = {k: v for k, v in opts.items() if k not in ("bed_source", "rain", "infiltration")}
+    qb = rain = beta = None
     if opts.get("bed_source"):
         g = I.rng(43)
         qb = g.normal(0.0, 1e-4, (sc.ny, sc.nx))
     if opts.get("rain"):
         g = I.rng(44)
         rain = g.uniform(0.0, 2e-4, (sc.ny, sc.nx))
+    if opts.get("infiltration"):
+        g = I.rng(45)
+        beta = g.uniform(0.0, 5e-3, (sc.ny, sc.nx))     # drains thin films within the run
     p0 = orc.Params(nx=sc.nx, ny=sc.ny, dx=sc.dx, **kw)
     st, t, _ = orc.run(p0, orc.State(sc.H, sc.Hu, sc.Hv, sc.b), sc.manning_per_cell(), 40, src=sc.src,
-                       qb=qb, hydro=orc.Hydrograph(sc.hydro_t, sc.hydro_Q), rain=rain)
+                       qb=qb, hydro=orc.Hydrograph(sc.hydro_t, sc.hydro_Q), rain=rain, beta=beta)
     sc.H, sc.Hu, sc.Hv, sc.b = st.H, st.Hu, st.Hv, st.b
-    worst = _per_step_parity(gpu, orc, sc, 30, bw=128, th=16, qb=qb, rain=rain, **kw)
+    worst = _per_step_parity(gpu, orc, sc, 30, bw=128, th=16, qb=qb, rain=rain, beta=beta, **kw)
     print("fp64 options", opts, "worst rel Linf:", worst)
 
 
