@@ -83,7 +83,7 @@ ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restr
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             const int4 w = items[it];
             __syncthreads();
-            step_tile<float, BW, true>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
+            step_tile<float, BW, true, true>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
         }
         if (!grid_sync(bar, expected, timeout_ns, status)) return;
         if (blockIdx.x == 0)

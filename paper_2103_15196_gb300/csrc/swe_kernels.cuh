@@ -420,7 +420,7 @@ template <typename T> __device__ inline T tab(const void *p, int i) { return rei
 //   row s-3, and the y-face (s-4|s-3).
 // Every read of a neighbour column refers to a row finished at an earlier
 // position, so one __syncthreads per position suffices.
-template <typename T, int BW, bool COHERENT> struct Sweep {
+template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
     StepSmem<T, BW> &S;
     const SweConst &c;
     const SweBufs &B;
@@ -544,14 +544,14 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
             const int r = s - 5;
             const T Hc = Hr<P, 5>()[o], bc = Br<P, 5>()[o];
             bool src = false;
-            if (c.nsrc > 0)
+            if (EXTRA && c.nsrc > 0)
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
             T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
-            if (c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
+            if (EXTRA && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
             T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
-            if (c.has_beta) {
+            if (EXTRA && c.has_beta) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
                 if (loss > hn) loss = hn > T(0) ? hn : T(0);
@@ -630,7 +630,9 @@ template <typename T, int BW, bool COHERENT> struct Sweep {
 // One step of one block (column band bx, row strip by).  COHERENT selects
 // L2-coherent reads of the state, census and bookkeeping, needed when other
 // blocks of the same (persistent) launch rewrote them since its start.
-template <typename T, int BW, bool COHERENT>
+// EXTRA compiles in the inflow, rain and infiltration terms of the update;
+// without it (no such term set) the kernel is smaller.
+template <typename T, int BW, bool COHERENT, bool EXTRA>
 __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, int bx, int by, StepSmem<T, BW> &S) {
     SweDev *dev = B.dev;
     const volatile SweDev *vdev = dev;
@@ -676,7 +678,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     if (t == 0) atomicAdd(&dev->cells_computed, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
 
     const K<T> k = load_k<T>(c, COHERENT ? const_cast<const SweDev *>(dev) : dev, COHERENT);
-    Sweep<T, BW, COHERENT> w(S, c, B, k);
+    Sweep<T, BW, COHERENT, EXTRA> w(S, c, B, k);
     w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
     w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
@@ -771,14 +773,14 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
 // One step: one CUDA block per grid block; CUDA block i runs entry i of the
 // work list (a column band x row strip), blocks past the list's end return at
 // once.  With every block listed this is one block per grid block in order.
-template <typename T, int BW>
+template <typename T, int BW, bool EXTRA>
 __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int i = blockIdx.x;
     if (i >= B.work[0]) return;
     const int tile = B.work[2 + i];
-    step_tile<T, BW, false>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+    step_tile<T, BW, false, EXTRA>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state

@@ -10,18 +10,25 @@ template <typename T> size_t step_smem_bytes(int bw) {
 }
 
 // One step: the work list of the blocks to run (compact_kernel), then one
-// CUDA block per grid block, the unlisted ones returning at once.
-template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+// CUDA block per grid block, the unlisted ones returning at once.  The kernel
+// variant without the inflow, rain and infiltration terms runs when none is
+// set.
+template <typename T, int BW, bool EXTRA> static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
     static bool configured = false;
     const size_t smem = sizeof(StepSmem<T, BW>);
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, BW, EXTRA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
-    step_kernel<T, BW><<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
+    step_kernel<T, BW, EXTRA><<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
     return cudaGetLastError();
+}
+
+template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+    const bool extra = c.nsrc > 0 || c.has_rain || c.has_beta;
+    return extra ? launch_step_v<T, BW, true>(c, b, s) : launch_step_v<T, BW, false>(c, b, s);
 }
 
 template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s) {
