@@ -151,15 +151,16 @@ template <typename T> struct K {  // step constants in the state precision
 
 // Grass discharge (Eq. 3) gated by the Shamov velocity (Eq. 5, written as
 // |v|^6 > C_Sh^6 d50^2 H); A_J constant or from Eq. 4.
-template <typename T>
+template <typename T, bool GEN = true>
 __device__ inline void grass(const SweConst &c, const K<T> &k, bool wet, T H, T ajn, T vx, T vy,
                              T &Jx, T &Jy, T &Ja) {
     Jx = T(0); Jy = T(0); Ja = T(0);
     if (!c.sediment_on || !wet) return;
     T s2 = vx * vx + vy * vy;
     if (!(s2 * s2 * s2 > k.ksh * H)) return;
-    T AJ = c.aj_mode == 1 ? ajn / ((k.sm1 * mm_sqrt(k.g * H)) * k.d50) : k.A_J;
-    T vm = c.m_is_2 ? s2 : mm_pow(s2, T(0.5) * k.m_exp);
+    // GEN = false compiles only the default laws (constant A_J, m = 2)
+    T AJ = (GEN && c.aj_mode == 1) ? ajn / ((k.sm1 * mm_sqrt(k.g * H)) * k.d50) : k.A_J;
+    T vm = (!GEN || c.m_is_2) ? s2 : mm_pow(s2, T(0.5) * k.m_exp);
     Jx = (AJ * vx) * vm;
     Jy = (AJ * vy) * vm;
     Ja = (AJ * vm) * mm_sqrt(s2);
@@ -377,7 +378,7 @@ __device__ inline void face_flux2(const SweConst &c, const K<T> &k, const T L[5]
 }
 
 // Per-cell terms of Eq. 7 and the census for a new state value.
-template <typename T>
+template <typename T, bool GEN = true>
 __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T hun, T hvn, T bn, T ajn,
                                       bool src, int &cnt, T &m0, T &m1, T &m2, unsigned &st) {
     const bool wet = is_wet(hn, c);
@@ -390,7 +391,7 @@ __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T 
         m0 = va > m0 ? va : m0;
         m1 = cs > m1 ? cs : m1;
         T jx, jy, ja;
-        grass<T>(c, k, true, hn, ajn, u, v, jx, jy, ja);
+        grass<T, GEN>(c, k, true, hn, ajn, u, v, jx, jy, ja);
         m2 = ja > m2 ? ja : m2;
     }
     if (!(hn >= -k.neg_tol)) st |= 2u;
@@ -507,7 +508,7 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
                 if (my != gn2_row) {
                     gn2_row = my;
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
-                    if (c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
+                    if (EXTRA && c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
                 }
                 const T HE = Hr<P, 2>()[o + 1], bE = Br<P, 2>()[o + 1];
                 const T HW = Hr<P, 2>()[o - 1], bW = Br<P, 2>()[o - 1];
@@ -534,7 +535,7 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
                 const T vat = mm_sqrt(vtx * vtx + vty * vty);
                 const T den2 = T(1) + k.dt * (cf * vat);
                 Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
-                grass<T>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
+                grass<T, EXTRA>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
             S.ux[PM2_4][o] = vtx; S.uy[PM2_4][o] = vty; S.wx[PM2_4][o] = wxv; S.wy[PM2_4][o] = wyv;
             S.jx[PM2_4][o] = jx; S.jy[PM2_4][o] = jy; S.ja[PM2_4][o] = ja;
@@ -565,11 +566,11 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
             const T bn = bc - k.cb * ((S.xf[PM5_2][3][o] - S.xf[PM5_2][3][o - 1]) + (G1[3] - G2[3]));
             CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
-            if (c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
+            if (EXTRA && c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
                 aj_row = r >> c.man_shift;
                 aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
             }
-            cell_epilogue2<T>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
+            cell_epilogue2<T, EXTRA>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
         }
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
@@ -630,8 +631,9 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
 // One step of one block (column band bx, row strip by).  COHERENT selects
 // L2-coherent reads of the state, census and bookkeeping, needed when other
 // blocks of the same (persistent) launch rewrote them since its start.
-// EXTRA compiles in the inflow, rain and infiltration terms of the update;
-// without it (no such term set) the kernel is smaller.
+// EXTRA compiles in the inflow, rain and infiltration terms of the update and
+// the general transport laws (A_J from Eq. 4, m != 2); without it (none of
+// these in use) the kernel is smaller.
 template <typename T, int BW, bool COHERENT, bool EXTRA>
 __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, int bx, int by, StepSmem<T, BW> &S) {
     SweDev *dev = B.dev;

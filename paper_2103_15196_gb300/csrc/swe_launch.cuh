@@ -11,8 +11,8 @@ template <typename T> size_t step_smem_bytes(int bw) {
 
 // One step: the work list of the blocks to run (compact_kernel), then one
 // CUDA block per grid block, the unlisted ones returning at once.  The kernel
-// variant without the inflow, rain and infiltration terms runs when none is
-// set.
+// variant without the inflow, rain and infiltration terms and the general
+// transport laws runs when none of them is in use.
 template <typename T, int BW, bool EXTRA> static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
     static bool configured = false;
     const size_t smem = sizeof(StepSmem<T, BW>);
@@ -27,7 +27,7 @@ template <typename T, int BW, bool EXTRA> static cudaError_t launch_step_v(const
 }
 
 template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
-    const bool extra = c.nsrc > 0 || c.has_rain || c.has_beta;
+    const bool extra = c.nsrc > 0 || c.has_rain || c.has_beta || c.aj_mode == 1 || !c.m_is_2;
     return extra ? launch_step_v<T, BW, true>(c, b, s) : launch_step_v<T, BW, false>(c, b, s);
 }
 
