@@ -73,7 +73,9 @@ __device__ bool grid_sync(unsigned *bar, unsigned expected, unsigned long long t
     return s_ok != 0;
 }
 
-template <int BW>
+// GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; the
+// sources are always compiled in (scenarios carry inflow).
+template <int BW, bool GEN>
 __global__ void __launch_bounds__(BW, 2)
 ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restrict__ items, int nitems,
                 int nsteps, unsigned *bar, unsigned expected, unsigned *status, unsigned long long timeout_ns) {
@@ -83,7 +85,7 @@ ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restr
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             const int4 w = items[it];
             __syncthreads();
-            step_tile<float, BW, true, true>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
+            step_tile<float, BW, true, true, GEN>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
         }
         if (!grid_sync(bar, expected, timeout_ns, status)) return;
         if (blockIdx.x == 0)
@@ -108,18 +110,19 @@ struct swe_ensemble {
     std::map<long long, cudaGraphExec_t> graphs;
     int nitems = 0;
     int grid = 0;            // co-resident blocks of the persistent kernel for bw
+    bool gen = false;        // some scenario uses the general transport laws
     bool graph_ok = true;    // false if this driver cannot capture the cooperative launch
 };
 
 namespace {
 
-template <int BW> int resident_blocks() {
+template <int BW, bool GEN> int resident_blocks() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = sizeof(StepSmem<float, BW>);
-    cudaFuncSetAttribute(ensemble_kernel<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_kernel<BW>, BW, smem);
+    cudaFuncSetAttribute(ensemble_kernel<BW, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_kernel<BW, GEN>, BW, smem);
     return std::max(1, per) * sms;
 }
 
@@ -162,7 +165,7 @@ swe_status upload(swe_ensemble *e) {
     return SWE_OK;
 }
 
-template <int BW> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
+template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
     const int grid = e->grid;
     const size_t smem = sizeof(StepSmem<float, BW>);
     cudaError_t err = cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned), e->stream);
@@ -179,12 +182,13 @@ template <int BW> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
     cfg.numAttrs = 1;
     const EnsScen *sc = e->d_scen;
     const int4 *it = e->d_items;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW>, sc, (int)e->members.size(), it, e->nitems, nsteps,
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN>, sc, (int)e->members.size(), it, e->nitems, nsteps,
                               e->d_bar, (unsigned)(grid + e->extra_arrivals), e->d_bar + 2, e->timeout_ns);
 }
 
 cudaError_t launch_any(swe_ensemble *e, int nsteps) {
-    return e->bw == 128 ? launch_persistent<128>(e, nsteps) : launch_persistent<256>(e, nsteps);
+    if (e->gen) return e->bw == 128 ? launch_persistent<128, true>(e, nsteps) : launch_persistent<256, true>(e, nsteps);
+    return e->bw == 128 ? launch_persistent<128, false>(e, nsteps) : launch_persistent<256, false>(e, nsteps);
 }
 
 // The graph of one persistent launch of `nsteps` steps (cached per count).
@@ -247,6 +251,7 @@ extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void 
     e->th = params[0].tile_rows ? params[0].tile_rows : 64;
     for (int k = 0; k < n; ++k) {
         swe_params p = params[k];
+        if (p.aj_mode == 1 || p.m_exp != 2.0) e->gen = true;
         p.block_cols = e->bw;
         p.tile_rows = e->th;
         swe_handle *h = nullptr;
@@ -288,7 +293,9 @@ extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
     if (nsteps == 0) return SWE_OK;
     swe_status s = upload(e);
     if (s != SWE_OK) return s;
-    if (e->grid == 0) e->grid = e->bw == 128 ? resident_blocks<128>() : resident_blocks<256>();
+    if (e->grid == 0)
+        e->grid = e->gen ? (e->bw == 128 ? resident_blocks<128, true>() : resident_blocks<256, true>())
+                         : (e->bw == 128 ? resident_blocks<128, false>() : resident_blocks<256, false>());
     // one persistent launch per call (split only beyond 2^30 steps)
     while (nsteps > 0) {
         const int chunk = (int)std::min<int64_t>(nsteps, 1 << 30);

@@ -421,7 +421,7 @@ template <typename T> __device__ inline T tab(const void *p, int i) { return rei
 //   row s-3, and the y-face (s-4|s-3).
 // Every read of a neighbour column refers to a row finished at an earlier
 // position, so one __syncthreads per position suffices.
-template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
+template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     StepSmem<T, BW> &S;
     const SweConst &c;
     const SweBufs &B;
@@ -508,7 +508,7 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
                 if (my != gn2_row) {
                     gn2_row = my;
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
-                    if (EXTRA && c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
+                    if (GEN && c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
                 }
                 const T HE = Hr<P, 2>()[o + 1], bE = Br<P, 2>()[o + 1];
                 const T HW = Hr<P, 2>()[o - 1], bW = Br<P, 2>()[o - 1];
@@ -535,7 +535,7 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
                 const T vat = mm_sqrt(vtx * vtx + vty * vty);
                 const T den2 = T(1) + k.dt * (cf * vat);
                 Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
-                grass<T, EXTRA>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
+                grass<T, GEN>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
             S.ux[PM2_4][o] = vtx; S.uy[PM2_4][o] = vty; S.wx[PM2_4][o] = wxv; S.wy[PM2_4][o] = wyv;
             S.jx[PM2_4][o] = jx; S.jy[PM2_4][o] = jy; S.ja[PM2_4][o] = ja;
@@ -545,14 +545,14 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
             const int r = s - 5;
             const T Hc = Hr<P, 5>()[o], bc = Br<P, 5>()[o];
             bool src = false;
-            if (EXTRA && c.nsrc > 0)
+            if (SRC && c.nsrc > 0)
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
             T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
-            if (EXTRA && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
+            if (SRC && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
             T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
-            if (EXTRA && c.has_beta) {
+            if (SRC && c.has_beta) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
                 if (loss > hn) loss = hn > T(0) ? hn : T(0);
@@ -566,11 +566,11 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
             const T bn = bc - k.cb * ((S.xf[PM5_2][3][o] - S.xf[PM5_2][3][o - 1]) + (G1[3] - G2[3]));
             CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
-            if (EXTRA && c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
+            if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
                 aj_row = r >> c.man_shift;
                 aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
             }
-            cell_epilogue2<T, EXTRA>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
+            cell_epilogue2<T, GEN>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
         }
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
@@ -631,10 +631,10 @@ template <typename T, int BW, bool COHERENT, bool EXTRA> struct Sweep {
 // One step of one block (column band bx, row strip by).  COHERENT selects
 // L2-coherent reads of the state, census and bookkeeping, needed when other
 // blocks of the same (persistent) launch rewrote them since its start.
-// EXTRA compiles in the inflow, rain and infiltration terms of the update and
-// the general transport laws (A_J from Eq. 4, m != 2); without it (none of
-// these in use) the kernel is smaller.
-template <typename T, int BW, bool COHERENT, bool EXTRA>
+// SRC compiles in the inflow, rain and infiltration terms of the update, GEN
+// the general transport laws (A_J from Eq. 4, m != 2); without them (not in
+// use) the kernel is markedly smaller, which its instruction fetch rewards.
+template <typename T, int BW, bool COHERENT, bool SRC, bool GEN>
 __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, int bx, int by, StepSmem<T, BW> &S) {
     SweDev *dev = B.dev;
     const volatile SweDev *vdev = dev;
@@ -680,7 +680,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     if (t == 0) atomicAdd(&dev->cells_computed, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
 
     const K<T> k = load_k<T>(c, COHERENT ? const_cast<const SweDev *>(dev) : dev, COHERENT);
-    Sweep<T, BW, COHERENT, EXTRA> w(S, c, B, k);
+    Sweep<T, BW, COHERENT, SRC, GEN> w(S, c, B, k);
     w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
     w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
@@ -775,14 +775,14 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
 // One step: one CUDA block per grid block; CUDA block i runs entry i of the
 // work list (a column band x row strip), blocks past the list's end return at
 // once.  With every block listed this is one block per grid block in order.
-template <typename T, int BW, bool EXTRA>
+template <typename T, int BW, bool SRC, bool GEN>
 __global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int i = blockIdx.x;
     if (i >= B.work[0]) return;
     const int tile = B.work[2 + i];
-    step_tile<T, BW, false, EXTRA>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+    step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state

@@ -11,24 +11,32 @@ template <typename T> size_t step_smem_bytes(int bw) {
 
 // One step: the work list of the blocks to run (compact_kernel), then one
 // CUDA block per grid block, the unlisted ones returning at once.  The kernel
-// variant without the inflow, rain and infiltration terms and the general
-// transport laws runs when none of them is in use.
-template <typename T, int BW, bool EXTRA> static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+// variant compiles only the terms in use: inflow, rain and infiltration
+// (SRC), the general transport laws (GEN).
+template <typename T, int BW, bool SRC, bool GEN>
+static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
     static bool configured = false;
     const size_t smem = sizeof(StepSmem<T, BW>);
+    auto kern = step_kernel<T, BW, SRC, GEN>;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, BW, EXTRA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
-    step_kernel<T, BW, EXTRA><<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
+    kern<<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
     return cudaGetLastError();
 }
 
+inline bool uses_sources(const SweConst &c) { return c.nsrc > 0 || c.has_rain || c.has_beta; }
+inline bool uses_general_laws(const SweConst &c) { return c.aj_mode == 1 || !c.m_is_2; }
+
 template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
-    const bool extra = c.nsrc > 0 || c.has_rain || c.has_beta || c.aj_mode == 1 || !c.m_is_2;
-    return extra ? launch_step_v<T, BW, true>(c, b, s) : launch_step_v<T, BW, false>(c, b, s);
+    // the FP64 build (parity) runs the general variant only
+    if constexpr (sizeof(T) == 8) return launch_step_v<T, BW, true, true>(c, b, s);
+    const bool src = uses_sources(c), gen = uses_general_laws(c);
+    if (src) return gen ? launch_step_v<T, BW, true, true>(c, b, s) : launch_step_v<T, BW, true, false>(c, b, s);
+    return gen ? launch_step_v<T, BW, false, true>(c, b, s) : launch_step_v<T, BW, false, false>(c, b, s);
 }
 
 template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s) {
