@@ -1206,13 +1206,9 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             if (err > bound) { st->mode = 1; st->takeover_window = w; }
         } else {                                                 // surrogate window
             if ((rc = first_step_and_predict()) != SWE_OK) break;
-            if (K / f > 1) {
-                if ((rc = swe_set_sediment(h, 0)) != SWE_OK) break;
-                rc = swe_run_steps(h, K / f - 1);
-                const swe_status r2 = swe_set_sediment(h, 1);
-                if (rc == SWE_OK) rc = r2;
-                if (rc != SWE_OK) break;
-            }
+            // the remaining water steps run the coupled step as it is: the bed
+            // they move is replaced by the prediction at the window's end
+            if (K / f > 1 && (rc = swe_run_steps(h, K / f - 1)) != SWE_OK) break;
             if ((rc = swe_get_time(h, &t1)) != SWE_OK) break;
             if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
             if ((rc = check_err(s)) != SWE_OK || (rc = launch_apply(s, h, k)) != SWE_OK) break;
