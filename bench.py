@@ -625,7 +625,7 @@ def run_ours(args):
                    "block": [dd["tile_x"], dd["tile_y"]]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<float,256>",
+                     "kernel": "step_kernel<float,256> (variant without source terms)",
                      "algorithmic_bytes_per_launch": alg_bytes_launch,
                      "note": "launch duration = timed region / K (includes the one-thread dt kernel)"},
         "issue": _issue_object(value, clk.summary()),
@@ -633,7 +633,7 @@ def run_ours(args):
                 "all_cell_equiv_GBps": BYTES_PER_CELL * n * n / (ms * 1e-3 / K) / 1e9,
                 "wet_cells_end": dd["wet_cells"], "t_end": dd["t"]},
         "e2e": e2e,
-        "gpu_launches": 2 * K,
+        "gpu_launches": 3 * K,   # per step: compact_kernel, step_kernel, between_kernel
         "clocks": clocks,
         "cpu_baseline": cb,
         "ensemble": ens,
