@@ -404,7 +404,7 @@ __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T 
 template <typename T, int BW> struct StepSmem {
     static constexpr int RW = BW + 4;
     T H[8][RW], b[8][RW];                       // state rows s-7..s
-    T u[4][RW], v[4][RW];                       // cell velocities v^n, rows s-3..s
+    T u[4][RW];                                 // cell velocity u^n, rows s-3..s (v^n: registers)
     T Hh[4][RW];                                // K4 particle depth H^{n+1/2}
     T ux[4][RW], uy[4][RW], wx[4][RW], wy[4][RW];  // K4 transport / K6 end velocity
     T jx[4][RW], jy[4][RW], ja[4][RW];          // Grass load from the transport velocity
@@ -434,6 +434,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     int gn2_row, aj_row;
     T gn2, ajo, aj_out;
     T qE[5], qN[5], G1[4], G2[4];
+    T vr[4];                // own-column ring of v^n (rows s-3..s): only this thread reads it
     int cnt;
     T m0, m1, m2;
     unsigned st;
@@ -488,11 +489,11 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             T u = T(0);
             if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
             S.u[P4][o] = u;
-            S.v[P4][o] = v_s;
+            vr[P4] = v_s;
         }
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
         if (FULL || (s - 1 >= y0 - 3 && s - 1 <= y1 + 2)) {
-            const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - S.v[PM2_4][o]));
+            const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - vr[PM2_4]));
             S.Hh[PM1_4][o] = Hr<P, 1>()[o] / A;
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
@@ -502,7 +503,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             const bool wet = is_wet(Hc, c);
             T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
             if (wet) {
-                const T bc = Br<P, 2>()[o], u = S.u[PM2_4][o], v = S.v[PM2_4][o];
+                const T bc = Br<P, 2>()[o], u = S.u[PM2_4][o], v = vr[PM2_4];
                 int sy;
                 const int my = reflect(r, c.ny, c.bc[2], c.bc[3], sy) >> c.man_shift;
                 if (my != gn2_row) {
@@ -694,7 +695,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
 #pragma unroll
     for (int q = 0; q < 5; ++q) { w.qE[q] = T(0); w.qN[q] = T(0); }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); }
+    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); w.vr[q] = T(0); }
     w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
         int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
@@ -776,7 +777,8 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
 // work list (a column band x row strip), blocks past the list's end return at
 // once.  With every block listed this is one block per grid block in order.
 template <typename T, int BW, bool SRC, bool GEN>
-__global__ void __launch_bounds__(BW, 2) step_kernel(SweConst c, SweBufs B) {
+// FP32: three blocks per SM (80 registers, 73 KB of shared memory each).
+__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? 3 : 1) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int i = blockIdx.x;

@@ -32,11 +32,13 @@ inline bool uses_sources(const SweConst &c) { return c.nsrc > 0 || c.has_rain ||
 inline bool uses_general_laws(const SweConst &c) { return c.aj_mode == 1 || !c.m_is_2; }
 
 template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
-    // the FP64 build (parity) runs the general variant only
-    if constexpr (sizeof(T) == 8) return launch_step_v<T, BW, true, true>(c, b, s);
-    const bool src = uses_sources(c), gen = uses_general_laws(c);
-    if (src) return gen ? launch_step_v<T, BW, true, true>(c, b, s) : launch_step_v<T, BW, true, false>(c, b, s);
-    return gen ? launch_step_v<T, BW, false, true>(c, b, s) : launch_step_v<T, BW, false, false>(c, b, s);
+    if constexpr (sizeof(T) == 8) {
+        return launch_step_v<T, BW, true, true>(c, b, s);   // the FP64 build (parity): the general variant
+    } else {
+        const bool src = uses_sources(c), gen = uses_general_laws(c);
+        if (src) return gen ? launch_step_v<T, BW, true, true>(c, b, s) : launch_step_v<T, BW, true, false>(c, b, s);
+        return gen ? launch_step_v<T, BW, false, true>(c, b, s) : launch_step_v<T, BW, false, false>(c, b, s);
+    }
 }
 
 template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s) {
