@@ -414,8 +414,10 @@ template <typename T, int BW> struct StepSmem {
 
 template <typename T> __device__ inline T tab(const void *p, int i) { return reinterpret_cast<const T *>(p)[i]; }
 
-// The sweep of one block.  pos<P>(s) runs the pipeline at sweep position s
-// with P = s mod 8 known at compile time (so every ring slot is a constant):
+// The sweep of one block.  pos<P>(s) runs the pipeline at sweep position s;
+// the sweep advances two positions per loop iteration, P = s mod 2 is known
+// at compile time and every ring row is a per-iteration bank base plus a
+// constant offset:
 //   load row s | K4 depth, row s-1 | K2 K4 K5 K6 + Grass, row s-2 |
 //   K8 update, row s-5 | x-faces, row s-4 | per-cell limited face states,
 //   row s-3, and the y-face (s-4|s-3).
@@ -434,29 +436,37 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     int gn2_row, aj_row;
     T gn2, ajo, aj_out;
     T qE[5], qN[5], G1[4], G2[4];
-    T vr[4];                // own-column ring of v^n (rows s-3..s): only this thread reads it
+    T vA[2], vB[2];         // own-column v^n of rows s-P, s-P+1 and of the two rows before
     int cnt;
     T m0, m1, m2;
     unsigned st;
     T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
     int asy, bsy;
-    T *Hc, *Hp, *bc, *bp;   // current / previous 4-row banks of the 8-row H and b rings
+    T *hb[4];               // 2-row banks of the 8-row H ring holding rows 2m-2j, 2m-2j+1
+    int q4c, q4o;           // offsets of the current / previous 2-row bank of the 4-row rings
 
-    // Row s-D of the 8-row ring, for a sweep position s = 4m + P: rows of the
-    // current group of four live in bank (m & 1), older ones in the other bank
-    // (rows s-8..s-5 of group m-2 share the current bank's slots).
+    // Ring row r lives in slot r mod 8 (H, b) or r mod 4 (the 4-row rings).
+    // For a sweep position s = 2m + P, row s-D = 2m + d with d = P - D, i.e.
+    // in the bank of rows 2(m + fd), 2(m + fd) + 1, fd = floor(d / 2).
+    template <int P, int D> struct FD {
+        static constexpr int v = (P - D) >= 0 ? (P - D) / 2 : -((1 - (P - D)) / 2);
+    };
     template <int P, int D> __device__ __forceinline__ T *Hr() const {
-        constexpr int d = P - D;
-        return ((d < 0 && d >= -4) ? Hp : Hc) + (d & 3) * StepSmem<T, BW>::RW;
+        return hb[-FD<P, D>::v] + ((P - D) & 1) * StepSmem<T, BW>::RW;
     }
-    template <int P, int D> __device__ __forceinline__ T *Br() const {
-        constexpr int d = P - D;
-        return ((d < 0 && d >= -4) ? bp : bc) + (d & 3) * StepSmem<T, BW>::RW;
+    template <int P, int D> __device__ __forceinline__ T *Br() const {   // b follows H in the ring struct
+        return Hr<P, D>() + 8 * StepSmem<T, BW>::RW;
+    }
+    template <int P, int D> __device__ __forceinline__ T *q4(T (&a)[4][StepSmem<T, BW>::RW]) const {
+        return &a[0][0] + ((FD<P, D>::v & 1) ? q4o : q4c) + ((P - D) & 1) * StepSmem<T, BW>::RW;
     }
     __device__ __forceinline__ void set_banks(int s) {
-        const int g = (s >> 2) & 1;
-        Hc = &S.H[4 * g][0]; Hp = &S.H[4 * (g ^ 1)][0];
-        bc = &S.b[4 * g][0]; bp = &S.b[4 * (g ^ 1)][0];
+        const int m = s >> 1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hb[j] = &S.H[2 * ((m - j) & 3)][0];
+        q4c = 2 * StepSmem<T, BW>::RW * (m & 1);
+        q4o = 2 * StepSmem<T, BW>::RW * ((m & 1) ^ 1);
+        vB[0] = vA[0]; vB[1] = vA[1];
     }
 
     __device__ Sweep(StepSmem<T, BW> &S_, const SweConst &c_, const SweBufs &B_, const K<T> &k_)
@@ -470,8 +480,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     // FULL: every stage's row is inside the strip (s in [y0 + 5, y1 + 3]), so
     // the row-range tests are dropped (the same arithmetic, fewer branches).
     template <int P, bool FULL> __device__ __forceinline__ void pos(int s) {
-        constexpr int P4 = P & 3, PM1_4 = (P + 3) & 3, PM2_4 = (P + 2) & 3, PM3_4 = (P + 1) & 3,
-                      PM4_4 = P & 3, PM5_4 = (P + 3) & 3;
+        static_assert(P == 0 || P == 1, "two positions per bank");
         constexpr int PM3_2 = (P + 1) & 1, PM4_2 = P & 1, PM5_2 = (P + 1) & 1;
         T v_s = T(0);
         // ---------------- load row s (ghost rows by even extension)
@@ -488,13 +497,13 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             Br<P, 0>()[o] = bb;
             T u = T(0);
             if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
-            S.u[P4][o] = u;
-            vr[P4] = v_s;
+            q4<P, 0>(S.u)[o] = u;
+            vA[P] = v_s;
         }
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
         if (FULL || (s - 1 >= y0 - 3 && s - 1 <= y1 + 2)) {
-            const T A = T(1) + k.c4 * ((S.u[PM1_4][o + 1] - S.u[PM1_4][o - 1]) + (v_s - vr[PM2_4]));
-            S.Hh[PM1_4][o] = Hr<P, 1>()[o] / A;
+            const T A = T(1) + k.c4 * ((q4<P, 1>(S.u)[o + 1] - q4<P, 1>(S.u)[o - 1]) + (v_s - vB[P]));
+            q4<P, 1>(S.Hh)[o] = Hr<P, 1>()[o] / A;
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
         if (FULL || (s - 2 >= y0 - 2 && s - 2 <= y1 + 1)) {
@@ -503,7 +512,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             const bool wet = is_wet(Hc, c);
             T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
             if (wet) {
-                const T bc = Br<P, 2>()[o], u = S.u[PM2_4][o], v = vr[PM2_4];
+                const T bc = Br<P, 2>()[o], u = q4<P, 2>(S.u)[o], v = vB[P];
                 int sy;
                 const int my = reflect(r, c.ny, c.bc[2], c.bc[3], sy) >> c.man_shift;
                 if (my != gn2_row) {
@@ -526,9 +535,9 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 const T den = T(1) + k.hdt * (cf * va);
                 Ar<T>::div2(u + k.hdt * ax, v + k.hdt * ay, den, vtx, vty);
                 // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
-                const T hc = S.Hh[PM2_4][o], ech = hc + bc;
-                const T hE = S.Hh[PM2_4][o + 1], hW = S.Hh[PM2_4][o - 1];
-                const T hN = S.Hh[PM1_4][o], hS = S.Hh[PM3_4][o];
+                const T hc = q4<P, 2>(S.Hh)[o], ech = hc + bc;
+                const T hE = q4<P, 2>(S.Hh)[o + 1], hW = q4<P, 2>(S.Hh)[o - 1];
+                const T hN = q4<P, 1>(S.Hh)[o], hS = q4<P, 3>(S.Hh)[o];
                 const T ratio = hc / Hc;
                 const T bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, wE, hW + bW, bW, wW);
                 const T byf = axis_force<T>(k, ech, ratio, hN + bN, bN, wN, hS + bS, bS, wS);
@@ -538,8 +547,8 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
                 grass<T, GEN>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
-            S.ux[PM2_4][o] = vtx; S.uy[PM2_4][o] = vty; S.wx[PM2_4][o] = wxv; S.wy[PM2_4][o] = wyv;
-            S.jx[PM2_4][o] = jx; S.jy[PM2_4][o] = jy; S.ja[PM2_4][o] = ja;
+            q4<P, 2>(S.ux)[o] = vtx; q4<P, 2>(S.uy)[o] = vty; q4<P, 2>(S.wx)[o] = wxv; q4<P, 2>(S.wy)[o] = wyv;
+            q4<P, 2>(S.jx)[o] = jx; q4<P, 2>(S.jy)[o] = jy; q4<P, 2>(S.ja)[o] = ja;
         }
         // ---------------- K8: update row s-5
         if ((FULL || (s - 5 >= y0 && s - 5 <= y1 - 1)) && out_lane) {
@@ -551,8 +560,8 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
             if (SRC && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
-            T hun = Hc * S.wx[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
-            T hvn = Hc * S.wy[PM5_4][o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
+            T hun = Hc * q4<P, 5>(S.wx)[o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
+            T hvn = Hc * q4<P, 5>(S.wy)[o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
             if (SRC && c.has_beta) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
@@ -582,8 +591,8 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 T R[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) R[q] = S.qw[PM4_2][q][o + 1];
-                face_flux2<T>(c, k, qE, R, wc, we, S.ux[PM4_4][o], S.ux[PM4_4][o + 1], S.jx[PM4_4][o],
-                              S.jx[PM4_4][o + 1], S.ja[PM4_4][o], S.ja[PM4_4][o + 1], Br<P, 4>()[o],
+                face_flux2<T>(c, k, qE, R, wc, we, q4<P, 4>(S.ux)[o], q4<P, 4>(S.ux)[o + 1], q4<P, 4>(S.jx)[o],
+                              q4<P, 4>(S.jx)[o + 1], q4<P, 4>(S.ja)[o], q4<P, 4>(S.ja)[o + 1], Br<P, 4>()[o],
                               Br<P, 4>()[o + 1], f0, f1, f2, f3);
             }
             S.xf[PM4_2][0][o] = f0; S.xf[PM4_2][1][o] = f1; S.xf[PM4_2][2][o] = f2; S.xf[PM4_2][3][o] = f3;
@@ -603,19 +612,19 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 // x direction: (H, eta, ux, wx, wy) at t-1, t, t+1
                 cell_faces<T>(Hm, H0, Hp, lo, hi); S.qw[PM3_2][0][o] = lo; qE[0] = hi;
                 cell_faces<T>(Hm + Br<P, 3>()[o - 1], e0, Hp + Br<P, 3>()[o + 1], lo, hi); S.qw[PM3_2][1][o] = lo; qE[1] = hi;
-                cell_faces<T>(S.ux[PM3_4][o - 1], S.ux[PM3_4][o], S.ux[PM3_4][o + 1], lo, hi); S.qw[PM3_2][2][o] = lo; qE[2] = hi;
-                cell_faces<T>(S.wx[PM3_4][o - 1], S.wx[PM3_4][o], S.wx[PM3_4][o + 1], lo, hi); S.qw[PM3_2][3][o] = lo; qE[3] = hi;
-                cell_faces<T>(S.wy[PM3_4][o - 1], S.wy[PM3_4][o], S.wy[PM3_4][o + 1], lo, hi); S.qw[PM3_2][4][o] = lo; qE[4] = hi;
+                cell_faces<T>(q4<P, 3>(S.ux)[o - 1], q4<P, 3>(S.ux)[o], q4<P, 3>(S.ux)[o + 1], lo, hi); S.qw[PM3_2][2][o] = lo; qE[2] = hi;
+                cell_faces<T>(q4<P, 3>(S.wx)[o - 1], q4<P, 3>(S.wx)[o], q4<P, 3>(S.wx)[o + 1], lo, hi); S.qw[PM3_2][3][o] = lo; qE[3] = hi;
+                cell_faces<T>(q4<P, 3>(S.wy)[o - 1], q4<P, 3>(S.wy)[o], q4<P, 3>(S.wy)[o + 1], lo, hi); S.qw[PM3_2][4][o] = lo; qE[4] = hi;
                 // y direction: (H, eta, uy, wx, wy) at rows r-1, r, r+1 (own column)
                 T qS[5], hn5[5];
                 cell_faces<T>(Hs, H0, Hn, qS[0], hn5[0]);
                 cell_faces<T>(Hs + Br<P, 4>()[o], e0, Hn + Br<P, 2>()[o], qS[1], hn5[1]);
-                cell_faces<T>(S.uy[PM4_4][o], S.uy[PM3_4][o], S.uy[PM2_4][o], qS[2], hn5[2]);
-                cell_faces<T>(S.wx[PM4_4][o], S.wx[PM3_4][o], S.wx[PM2_4][o], qS[3], hn5[3]);
-                cell_faces<T>(S.wy[PM4_4][o], S.wy[PM3_4][o], S.wy[PM2_4][o], qS[4], hn5[4]);
+                cell_faces<T>(q4<P, 4>(S.uy)[o], q4<P, 3>(S.uy)[o], q4<P, 2>(S.uy)[o], qS[2], hn5[2]);
+                cell_faces<T>(q4<P, 4>(S.wx)[o], q4<P, 3>(S.wx)[o], q4<P, 2>(S.wx)[o], qS[3], hn5[3]);
+                cell_faces<T>(q4<P, 4>(S.wy)[o], q4<P, 3>(S.wy)[o], q4<P, 2>(S.wy)[o], qS[4], hn5[4]);
                 if ((FULL || s - 3 >= y0) && (ws || w0))
-                    face_flux2<T>(c, k, qN, qS, ws, w0, S.uy[PM4_4][o], S.uy[PM3_4][o], S.jy[PM4_4][o],
-                                  S.jy[PM3_4][o], S.ja[PM4_4][o], S.ja[PM3_4][o], Br<P, 4>()[o], b0,
+                    face_flux2<T>(c, k, qN, qS, ws, w0, q4<P, 4>(S.uy)[o], q4<P, 3>(S.uy)[o], q4<P, 4>(S.jy)[o],
+                                  q4<P, 3>(S.jy)[o], q4<P, 4>(S.ja)[o], q4<P, 3>(S.ja)[o], Br<P, 4>()[o], b0,
                                   G[0], G[1], G[2], G[3]);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) qN[q] = hn5[q];
@@ -695,7 +704,8 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
 #pragma unroll
     for (int q = 0; q < 5; ++q) { w.qE[q] = T(0); w.qN[q] = T(0); }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); w.vr[q] = T(0); }
+    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); }
+    w.vA[0] = w.vA[1] = T(0);
     w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
         int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
@@ -703,19 +713,15 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
         yy = reflect(y0 - 3, c.ny, c.bc[2], c.bc[3], w.bsy);
         w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
-    // sweep positions y0-8 .. y1+4 in groups of 4 (y0 is a multiple of 8)
-    for (int s = y0 - 8; s <= y1 + 4; s += 4) {
+    // sweep positions y0-8 .. y1+4 in pairs (y0 is a multiple of 8)
+    for (int s = y0 - 8; s <= y1 + 4; s += 2) {
         w.set_banks(s);
-        if (s >= y0 + 5 && s + 3 <= y1 + 3) {
+        if (s >= y0 + 5 && s + 1 <= y1 + 3) {
             w.template pos<0, true>(s);
             w.template pos<1, true>(s + 1);
-            w.template pos<2, true>(s + 2);
-            w.template pos<3, true>(s + 3);
         } else {
             w.template pos<0, false>(s);
             w.template pos<1, false>(s + 1);
-            w.template pos<2, false>(s + 2);
-            w.template pos<3, false>(s + 3);
         }
     }
     block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
