@@ -313,9 +313,10 @@ template <> struct Ar<float> {
         x = a * r; y = b * r;
     }
     __device__ static inline float pow43(float x) { return exp2f(1.33333333f * log2f(x)); }
+    // the median of (a, b, 0): 0 unless a and b share a sign, else the one
+    // nearer zero (four min/max, no branch)
     __device__ static inline float minmod(float a, float b) {
-        const float m = fminf(fabsf(a), fabsf(b));
-        return (a * b > 0.f) ? copysignf(m, a) : 0.f;
+        return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
     }
 };
 
