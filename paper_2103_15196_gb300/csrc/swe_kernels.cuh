@@ -401,16 +401,20 @@ __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T 
 
 // Shared-memory rings; each row is padded by 2 entries on both sides so the
 // edge threads' out-of-block neighbour reads stay in bounds (those threads'
-// results are never used).
+// results are never used).  Quantities read together are stored together
+// (V2: 8 B in FP32, V4: 16 B), so one shared-memory instruction moves them.
+template <typename T> struct alignas(2 * sizeof(T)) V2 { T x, y; };
+template <typename T> struct alignas(4 * sizeof(T) < 16 ? 4 * sizeof(T) : 16) V4 { T a, b, c, d; };
+
 template <typename T, int BW> struct StepSmem {
     static constexpr int RW = BW + 4;
-    T H[8][RW], b[8][RW];                       // state rows s-7..s
-    T u[4][RW];                                 // cell velocity u^n, rows s-3..s (v^n: registers)
-    T Hh[4][RW];                                // K4 particle depth H^{n+1/2}
-    T ux[4][RW], uy[4][RW], wx[4][RW], wy[4][RW];  // K4 transport / K6 end velocity
-    T jx[4][RW], jy[4][RW], ja[4][RW];          // Grass load from the transport velocity
-    T qw[2][5][RW];                             // x-direction minus-face states (H, eta, ux, wx, wy)
-    T xf[2][4][RW];                             // x-face fluxes (face t|t+1): mass, x-mom, y-mom, Exner
+    V2<T> hb[8][RW];                    // state (H, b), rows s-7..s
+    T u[4][RW];                         // cell velocity u^n, rows s-3..s (v^n: registers)
+    V2<T> hj[4][RW];                    // (K4 particle depth H^{n+1/2}, Grass |J|)
+    V2<T> U[4][RW], W[4][RW], J[4][RW]; // K4 transport velocity, K6 end velocity, Grass load (x, y)
+    V4<T> qw[2][RW];                    // x-direction minus-face states (H, eta, ux, wx) ...
+    T qy[2][RW];                        // ... and wy
+    V4<T> xf[2][RW];                    // x-face fluxes (face t|t+1): mass, x-mom, y-mom, Exner
 };
 
 template <typename T> __device__ inline T tab(const void *p, int i) { return reinterpret_cast<const T *>(p)[i]; }
@@ -425,6 +429,7 @@ template <typename T> __device__ inline T tab(const void *p, int i) { return rei
 // Every read of a neighbour column refers to a row finished at an earlier
 // position, so one __syncthreads per position suffices.
 template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
+    static constexpr int RW = StepSmem<T, BW>::RW;
     StepSmem<T, BW> &S;
     const SweConst &c;
     const SweBufs &B;
@@ -443,7 +448,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     unsigned st;
     T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
     int asy, bsy;
-    T *hb[4];               // 2-row banks of the 8-row H ring holding rows 2m-2j, 2m-2j+1
+    V2<T> *hbk[4];          // 2-row banks of the 8-row (H, b) ring holding rows 2m-2j, 2m-2j+1
     int q4c, q4o;           // offsets of the current / previous 2-row bank of the 4-row rings
 
     // Ring row r lives in slot r mod 8 (H, b) or r mod 4 (the 4-row rings).
@@ -452,21 +457,18 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     template <int P, int D> struct FD {
         static constexpr int v = (P - D) >= 0 ? (P - D) / 2 : -((1 - (P - D)) / 2);
     };
-    template <int P, int D> __device__ __forceinline__ T *Hr() const {
-        return hb[-FD<P, D>::v] + ((P - D) & 1) * StepSmem<T, BW>::RW;
+    template <int P, int D> __device__ __forceinline__ V2<T> *HB() const {
+        return hbk[-FD<P, D>::v] + ((P - D) & 1) * RW;
     }
-    template <int P, int D> __device__ __forceinline__ T *Br() const {   // b follows H in the ring struct
-        return Hr<P, D>() + 8 * StepSmem<T, BW>::RW;
-    }
-    template <int P, int D> __device__ __forceinline__ T *q4(T (&a)[4][StepSmem<T, BW>::RW]) const {
-        return &a[0][0] + ((FD<P, D>::v & 1) ? q4o : q4c) + ((P - D) & 1) * StepSmem<T, BW>::RW;
+    template <int P, int D, typename E> __device__ __forceinline__ E *q4(E (&a)[4][RW]) const {
+        return &a[0][0] + ((FD<P, D>::v & 1) ? q4o : q4c) + ((P - D) & 1) * RW;
     }
     __device__ __forceinline__ void set_banks(int s) {
         const int m = s >> 1;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) hb[j] = &S.H[2 * ((m - j) & 3)][0];
-        q4c = 2 * StepSmem<T, BW>::RW * (m & 1);
-        q4o = 2 * StepSmem<T, BW>::RW * ((m & 1) ^ 1);
+        for (int j = 0; j < 4; ++j) hbk[j] = &S.hb[2 * ((m - j) & 3)][0];
+        q4c = 2 * RW * (m & 1);
+        q4o = 2 * RW * ((m & 1) ^ 1);
         vB[0] = vA[0]; vB[1] = vA[1];
     }
 
@@ -494,8 +496,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
             const bool wet = is_wet(H, c);
-            Hr<P, 0>()[o] = H;
-            Br<P, 0>()[o] = bb;
+            HB<P, 0>()[o] = V2<T>{H, bb};
             T u = T(0);
             if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
             q4<P, 0>(S.u)[o] = u;
@@ -504,16 +505,17 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
         if (FULL || (s - 1 >= y0 - 3 && s - 1 <= y1 + 2)) {
             const T A = T(1) + k.c4 * ((q4<P, 1>(S.u)[o + 1] - q4<P, 1>(S.u)[o - 1]) + (v_s - vB[P]));
-            q4<P, 1>(S.Hh)[o] = Hr<P, 1>()[o] / A;
+            q4<P, 1>(S.hj)[o].x = HB<P, 1>()[o].x / A;
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
         if (FULL || (s - 2 >= y0 - 2 && s - 2 <= y1 + 1)) {
             const int r = s - 2;
-            const T Hc = Hr<P, 2>()[o];
+            const V2<T> C = HB<P, 2>()[o];
+            const T Hc = C.x;
             const bool wet = is_wet(Hc, c);
             T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
             if (wet) {
-                const T bc = Br<P, 2>()[o], u = q4<P, 2>(S.u)[o], v = vB[P];
+                const T bc = C.y, u = q4<P, 2>(S.u)[o], v = vB[P];
                 int sy;
                 const int my = reflect(r, c.ny, c.bc[2], c.bc[3], sy) >> c.man_shift;
                 if (my != gn2_row) {
@@ -521,10 +523,9 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
                     if (GEN && c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
                 }
-                const T HE = Hr<P, 2>()[o + 1], bE = Br<P, 2>()[o + 1];
-                const T HW = Hr<P, 2>()[o - 1], bW = Br<P, 2>()[o - 1];
-                const T HN = Hr<P, 1>()[o], bN = Br<P, 1>()[o];
-                const T HS = Hr<P, 3>()[o], bS = Br<P, 3>()[o];
+                const V2<T> E = HB<P, 2>()[o + 1], Wc = HB<P, 2>()[o - 1];
+                const V2<T> N = HB<P, 1>()[o], Sc = HB<P, 3>()[o];
+                const T HE = E.x, bE = E.y, HW = Wc.x, bW = Wc.y, HN = N.x, bN = N.y, HS = Sc.x, bS = Sc.y;
                 const bool wE = is_wet(HE, c), wW = is_wet(HW, c), wN = is_wet(HN, c), wS = is_wet(HS, c);
                 // K2: forces at t_n
                 const T ec = Hc + bc;
@@ -536,9 +537,9 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 const T den = T(1) + k.hdt * (cf * va);
                 Ar<T>::div2(u + k.hdt * ax, v + k.hdt * ay, den, vtx, vty);
                 // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
-                const T hc = q4<P, 2>(S.Hh)[o], ech = hc + bc;
-                const T hE = q4<P, 2>(S.Hh)[o + 1], hW = q4<P, 2>(S.Hh)[o - 1];
-                const T hN = q4<P, 1>(S.Hh)[o], hS = q4<P, 3>(S.Hh)[o];
+                const T hc = q4<P, 2>(S.hj)[o].x, ech = hc + bc;
+                const T hE = q4<P, 2>(S.hj)[o + 1].x, hW = q4<P, 2>(S.hj)[o - 1].x;
+                const T hN = q4<P, 1>(S.hj)[o].x, hS = q4<P, 3>(S.hj)[o].x;
                 const T ratio = hc / Hc;
                 const T bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, wE, hW + bW, bW, wW);
                 const T byf = axis_force<T>(k, ech, ratio, hN + bN, bN, wN, hS + bS, bS, wS);
@@ -548,21 +549,26 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
                 grass<T, GEN>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
-            q4<P, 2>(S.ux)[o] = vtx; q4<P, 2>(S.uy)[o] = vty; q4<P, 2>(S.wx)[o] = wxv; q4<P, 2>(S.wy)[o] = wyv;
-            q4<P, 2>(S.jx)[o] = jx; q4<P, 2>(S.jy)[o] = jy; q4<P, 2>(S.ja)[o] = ja;
+            q4<P, 2>(S.U)[o] = V2<T>{vtx, vty};
+            q4<P, 2>(S.W)[o] = V2<T>{wxv, wyv};
+            q4<P, 2>(S.J)[o] = V2<T>{jx, jy};
+            q4<P, 2>(S.hj)[o].y = ja;
         }
         // ---------------- K8: update row s-5
         if ((FULL || (s - 5 >= y0 && s - 5 <= y1 - 1)) && out_lane) {
             const int r = s - 5;
-            const T Hc = Hr<P, 5>()[o], bc = Br<P, 5>()[o];
+            const V2<T> C = HB<P, 5>()[o];
+            const T Hc = C.x, bc = C.y;
             bool src = false;
             if (SRC && c.nsrc > 0)
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
-            T hn = Hc - k.dtdx * ((S.xf[PM5_2][0][o] - S.xf[PM5_2][0][o - 1]) + (G1[0] - G2[0]));
+            const V4<T> f = S.xf[PM5_2][o], fw = S.xf[PM5_2][o - 1];
+            const V2<T> w = q4<P, 5>(S.W)[o];
+            T hn = Hc - k.dtdx * ((f.a - fw.a) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
             if (SRC && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
-            T hun = Hc * q4<P, 5>(S.wx)[o] - k.dtdx * ((S.xf[PM5_2][1][o] - S.xf[PM5_2][1][o - 1]) + (G1[1] - G2[1]));
-            T hvn = Hc * q4<P, 5>(S.wy)[o] - k.dtdx * ((S.xf[PM5_2][2][o] - S.xf[PM5_2][2][o - 1]) + (G1[2] - G2[2]));
+            T hun = Hc * w.x - k.dtdx * ((f.b - fw.b) + (G1[1] - G2[1]));
+            T hvn = Hc * w.y - k.dtdx * ((f.c - fw.c) + (G1[2] - G2[2]));
             if (SRC && c.has_beta) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
@@ -575,7 +581,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 }
             }
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
-            const T bn = bc - k.cb * ((S.xf[PM5_2][3][o] - S.xf[PM5_2][3][o - 1]) + (G1[3] - G2[3]));
+            const T bn = bc - k.cb * ((f.d - fw.d) + (G1[3] - G2[3]));
             CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
             if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
                 aj_row = r >> c.man_shift;
@@ -586,47 +592,53 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
         if (FULL || (s - 4 >= y0 && s - 4 <= y1 - 1)) {
-            const bool wc = is_wet(Hr<P, 4>()[o], c), we = is_wet(Hr<P, 4>()[o + 1], c);
+            const V2<T> C = HB<P, 4>()[o], E = HB<P, 4>()[o + 1];
+            const bool wc = is_wet(C.x, c), we = is_wet(E.x, c);
             T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
             if (wc || we) {
-                T R[5];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) R[q] = S.qw[PM4_2][q][o + 1];
-                face_flux2<T>(c, k, qE, R, wc, we, q4<P, 4>(S.ux)[o], q4<P, 4>(S.ux)[o + 1], q4<P, 4>(S.jx)[o],
-                              q4<P, 4>(S.jx)[o + 1], q4<P, 4>(S.ja)[o], q4<P, 4>(S.ja)[o + 1], Br<P, 4>()[o],
-                              Br<P, 4>()[o + 1], f0, f1, f2, f3);
+                const V4<T> q = S.qw[PM4_2][o + 1];
+                const T R[5] = {q.a, q.b, q.c, q.d, S.qy[PM4_2][o + 1]};
+                const V2<T> Uc = q4<P, 4>(S.U)[o], Ue = q4<P, 4>(S.U)[o + 1];
+                const V2<T> Jc = q4<P, 4>(S.J)[o], Je = q4<P, 4>(S.J)[o + 1];
+                face_flux2<T>(c, k, qE, R, wc, we, Uc.x, Ue.x, Jc.x, Je.x, q4<P, 4>(S.hj)[o].y,
+                              q4<P, 4>(S.hj)[o + 1].y, C.y, E.y, f0, f1, f2, f3);
             }
-            S.xf[PM4_2][0][o] = f0; S.xf[PM4_2][1][o] = f1; S.xf[PM4_2][2][o] = f2; S.xf[PM4_2][3][o] = f3;
+            S.xf[PM4_2][o] = V4<T>{f0, f1, f2, f3};
         }
         // ---------------- per-cell limited face states (K7 reconstruction), row s-3,
         // and the y-face (s-4 | s-3)
         if (FULL || (s - 3 >= y0 - 1 && s - 3 <= y1)) {
-            const T H0 = Hr<P, 3>()[o], b0 = Br<P, 3>()[o];
-            const T Hm = Hr<P, 3>()[o - 1], Hp = Hr<P, 3>()[o + 1];
-            const T Hs = Hr<P, 4>()[o], Hn = Hr<P, 2>()[o];
+            const V2<T> C = HB<P, 3>()[o], Wc = HB<P, 3>()[o - 1], E = HB<P, 3>()[o + 1];
+            const V2<T> Sc = HB<P, 4>()[o], N = HB<P, 2>()[o];
+            const T H0 = C.x, b0 = C.y, Hm = Wc.x, Hp = E.x, Hs = Sc.x, Hn = N.x;
             const bool w0 = is_wet(H0, c), ws = is_wet(Hs, c);
             const bool need = w0 || ws || is_wet(Hm, c) || is_wet(Hp, c) || is_wet(Hn, c);
             T G[4] = {T(0), T(0), T(0), T(0)};
             if (need) {
                 const T e0 = H0 + b0;
-                T lo, hi;
+                T lo, hi, lo2, hi2;
                 // x direction: (H, eta, ux, wx, wy) at t-1, t, t+1
-                cell_faces<T>(Hm, H0, Hp, lo, hi); S.qw[PM3_2][0][o] = lo; qE[0] = hi;
-                cell_faces<T>(Hm + Br<P, 3>()[o - 1], e0, Hp + Br<P, 3>()[o + 1], lo, hi); S.qw[PM3_2][1][o] = lo; qE[1] = hi;
-                cell_faces<T>(q4<P, 3>(S.ux)[o - 1], q4<P, 3>(S.ux)[o], q4<P, 3>(S.ux)[o + 1], lo, hi); S.qw[PM3_2][2][o] = lo; qE[2] = hi;
-                cell_faces<T>(q4<P, 3>(S.wx)[o - 1], q4<P, 3>(S.wx)[o], q4<P, 3>(S.wx)[o + 1], lo, hi); S.qw[PM3_2][3][o] = lo; qE[3] = hi;
-                cell_faces<T>(q4<P, 3>(S.wy)[o - 1], q4<P, 3>(S.wy)[o], q4<P, 3>(S.wy)[o + 1], lo, hi); S.qw[PM3_2][4][o] = lo; qE[4] = hi;
+                const V2<T> U3m = q4<P, 3>(S.U)[o - 1], U3 = q4<P, 3>(S.U)[o], U3p = q4<P, 3>(S.U)[o + 1];
+                const V2<T> W3m = q4<P, 3>(S.W)[o - 1], W3 = q4<P, 3>(S.W)[o], W3p = q4<P, 3>(S.W)[o + 1];
+                cell_faces<T>(Hm, H0, Hp, lo, hi); qE[0] = hi;
+                cell_faces<T>(Hm + Wc.y, e0, Hp + E.y, lo2, hi); qE[1] = hi;
+                T lo3, lo4;
+                cell_faces<T>(U3m.x, U3.x, U3p.x, lo3, hi); qE[2] = hi;
+                cell_faces<T>(W3m.x, W3.x, W3p.x, lo4, hi); qE[3] = hi;
+                S.qw[PM3_2][o] = V4<T>{lo, lo2, lo3, lo4};
+                cell_faces<T>(W3m.y, W3.y, W3p.y, lo, hi); S.qy[PM3_2][o] = lo; qE[4] = hi;
                 // y direction: (H, eta, uy, wx, wy) at rows r-1, r, r+1 (own column)
+                const V2<T> U4 = q4<P, 4>(S.U)[o], U2 = q4<P, 2>(S.U)[o];
+                const V2<T> W4 = q4<P, 4>(S.W)[o], W2 = q4<P, 2>(S.W)[o];
                 T qS[5], hn5[5];
                 cell_faces<T>(Hs, H0, Hn, qS[0], hn5[0]);
-                cell_faces<T>(Hs + Br<P, 4>()[o], e0, Hn + Br<P, 2>()[o], qS[1], hn5[1]);
-                cell_faces<T>(q4<P, 4>(S.uy)[o], q4<P, 3>(S.uy)[o], q4<P, 2>(S.uy)[o], qS[2], hn5[2]);
-                cell_faces<T>(q4<P, 4>(S.wx)[o], q4<P, 3>(S.wx)[o], q4<P, 2>(S.wx)[o], qS[3], hn5[3]);
-                cell_faces<T>(q4<P, 4>(S.wy)[o], q4<P, 3>(S.wy)[o], q4<P, 2>(S.wy)[o], qS[4], hn5[4]);
+                cell_faces<T>(Hs + Sc.y, e0, Hn + N.y, qS[1], hn5[1]);
+                cell_faces<T>(U4.y, U3.y, U2.y, qS[2], hn5[2]);
+                cell_faces<T>(W4.x, W3.x, W2.x, qS[3], hn5[3]);
+                cell_faces<T>(W4.y, W3.y, W2.y, qS[4], hn5[4]);
                 if ((FULL || s - 3 >= y0) && (ws || w0))
-                    face_flux2<T>(c, k, qN, qS, ws, w0, q4<P, 4>(S.uy)[o], q4<P, 3>(S.uy)[o], q4<P, 4>(S.jy)[o],
-                                  q4<P, 3>(S.jy)[o], q4<P, 4>(S.ja)[o], q4<P, 3>(S.ja)[o], Br<P, 4>()[o], b0,
-                                  G[0], G[1], G[2], G[3]);
+                    face_flux2<T>(c, k, qN, qS, ws, w0, U4.y, U3.y, q4<P, 4>(S.J)[o].y, q4<P, 3>(S.J)[o].y,
+                                  q4<P, 4>(S.hj)[o].y, q4<P, 3>(S.hj)[o].y, Sc.y, b0, G[0], G[1], G[2], G[3]);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) qN[q] = hn5[q];
             }
