@@ -795,9 +795,11 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
 // One step: one CUDA block per grid block; CUDA block i runs entry i of the
 // work list (a column band x row strip), blocks past the list's end return at
 // once.  With every block listed this is one block per grid block in order.
+// FP32: three blocks per SM (80 registers, 73 KB of shared memory each); two
+// for the variants with source terms or the general laws, whose sweep does
+// not fit 80 registers without spills.
 template <typename T, int BW, bool SRC, bool GEN>
-// FP32: three blocks per SM (80 registers, 73 KB of shared memory each).
-__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? 3 : 1) step_kernel(SweConst c, SweBufs B) {
+__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? ((SRC || GEN) ? 2 : 3) : 1) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int i = blockIdx.x;
