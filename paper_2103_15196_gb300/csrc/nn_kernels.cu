@@ -677,6 +677,148 @@ __global__ void apply_bed(float4 *__restrict__ state, int nx, int ny, int T, int
     }
 }
 
+// ---- prediction on active halo tiles (the surrogate windows)
+//
+// The network is fully convolutional with a receptive field of kHalo cells
+// (six 3x3 layers), so a cell's prediction needs only the kHalo-cell
+// neighbourhood.  The domain is cut into interior tiles of kTC x kTC cells;
+// the network runs only on the tiles whose activity mask holds a 1 (where it
+// is all zero the output m (z + bias + p) is exactly 0), each as a kTI x kTI
+// image of the interior and a kHalo-cell margin from its neighbours (zeros
+// beyond the domain, as for the whole-domain images).
+constexpr int kTI = 128;
+constexpr int kHalo = 6;
+constexpr int kTC = kTI - 2 * kHalo;
+
+// chg: 1 where the bed differs from the saved bed (row-major); pcell: the
+// linear extrapolation (b - b_saved) / norm[7] rounded to BF16 as the network
+// reads it (tile layout of the saved bed).
+__global__ void bed_change(const float4 *__restrict__ state, int nx, int ny, int T, int ntx,
+                           const float *__restrict__ bsave, const float *__restrict__ norm, uint8_t *__restrict__ chg,
+                           float *__restrict__ pcell) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        const size_t j = tile_index(x, y, T, ntx);
+        const float b = state[i].w, b0 = bsave[j];
+        chg[i] = b != b0;
+        pcell[j] = __bfloat162float(__float2bfloat16((b - b0) / norm[7]));
+    }
+}
+
+// Row pass of the activity mask, row-major: actr[y][x] = 1 if a cell of row y
+// within kActR columns of x changed its bed.
+__global__ void act_rows_rm(const uint8_t *__restrict__ chg, int nx, int ny, uint8_t *__restrict__ actr) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        uint8_t a = 0;
+        for (int xx = max(0, x - kActR); xx <= min(nx - 1, x + kActR); ++xx) a |= chg[(size_t)y * nx + xx];
+        actr[i] = a;
+    }
+}
+
+// flag[tile] = 1 for the interior tiles with a 1 in their activity mask: a
+// row-dilated 1 in one of their columns within kActR rows of their rows.
+__global__ void tile_flags(const uint8_t *__restrict__ actr, int nx, int ny, int ntcx, int ntcy, int *__restrict__ flag) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (!actr[i]) continue;
+        const int y = (int)(i / nx), x = (int)(i % nx), tx = x / kTC;
+        for (int ty = max(0, (y - kActR) / kTC); ty <= min(ntcy - 1, (y + kActR) / kTC); ++ty)
+            if (y >= ty * kTC - kActR && y < ty * kTC + kTC + kActR) flag[ty * ntcx + tx] = 1;
+    }
+}
+
+// The active tiles in order (list[0..count)) and each tile's place in that
+// list (slot, -1 for an inactive tile); clears the flags.  One block of 1024.
+__global__ void __launch_bounds__(1024) compact_tiles(int *__restrict__ flag, int nt, int *__restrict__ list,
+                                                      int *__restrict__ slot, int *__restrict__ count) {
+    __shared__ int wsum[32];
+    __shared__ int base, chunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < nt; t0 += 1024) {
+        const int t = t0 + (int)threadIdx.x;
+        const bool on = t < nt && flag[t] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
+            chunk = acc;
+        }
+        __syncthreads();
+        if (t < nt) {
+            const int k = on ? base + wsum[w] + __popc(m & ((1u << lane) - 1u)) : -1;
+            slot[t] = k;
+            if (on) list[k] = t;
+            flag[t] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += chunk;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+// Network input (NHWC8 BF16, the channels of pack_state) of the active tiles
+// list[first .. first + nimg): kTI x kTI pixels each.
+__global__ void gather_tiles(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ norm,
+                             float eps, float ksh, const float *__restrict__ pcell, const uint8_t *__restrict__ actr,
+                             const int *__restrict__ list, int first, int nimg, int ntcx, __nv_bfloat16 *__restrict__ X) {
+    const size_t total = (size_t)nimg * kTI * kTI;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / (kTI * kTI)), r = (int)(i % (kTI * kTI));
+        const int tile = list[first + b];
+        const int y = (tile / ntcx) * kTC - kHalo + r / kTI, x = (tile % ntcx) * kTC - kHalo + r % kTI;
+        __align__(16) __nv_bfloat16 o[8];
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (x >= 0 && y >= 0 && x < nx && y < ny) {
+            const float4 c = state[(size_t)y * nx + x];
+            f[0] = (c.x - norm[0]) / norm[1];
+            f[1] = (c.w - norm[2]) / norm[3];
+            if (c.x > eps) {
+                const float u = c.y / c.x, v = c.z / c.x, s2 = u * u + v * v;
+                f[2] = u / norm[4];
+                f[3] = v / norm[4];
+                if (s2 * s2 * s2 > ksh * c.x) { f[4] = u * s2 / norm[5]; f[5] = v * s2 / norm[5]; }
+            }
+            f[6] = pcell[tile_index(x, y, T, ntx)];
+            uint8_t a = 0;
+            for (int yy = max(0, y - kActR); yy <= min(ny - 1, y + kActR); ++yy) a |= actr[(size_t)yy * nx + x];
+            f[7] = a ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16(f[j]);
+        reinterpret_cast<uint4 *>(X)[i] = reinterpret_cast<uint4 *>(o)[0];
+    }
+}
+
+// The prediction of every cell (tile layout of the saved bed): the interior
+// pixels of the images of list[first .. first + nimg) (out: nimg x kTI x kTI),
+// 0 for the cells of inactive tiles (written with the first chunk).
+__global__ void scatter_pred(int nx, int ny, int T, int ntx, const float *__restrict__ out, const int *__restrict__ slot,
+                             int ntcx, int first, int nimg, float *__restrict__ predc) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        const int ty = y / kTC, tx = x / kTC;
+        const int sl = slot[ty * ntcx + tx];
+        float v;
+        if (sl < 0) {
+            if (first != 0) continue;
+            v = 0.f;
+        } else {
+            if (sl < first || sl >= first + nimg) continue;
+            v = out[((size_t)(sl - first) * kTI + (y - ty * kTC + kHalo)) * kTI + (x - tx * kTC + kHalo)];
+        }
+        predc[tile_index(x, y, T, ntx)] = v;
+    }
+}
+
 }  // namespace swe_nn
 
 // ======================================================================
@@ -721,6 +863,12 @@ struct swe_surrogate {
     long adam_t = 0;
     std::vector<void *> allocs;
     uint8_t *act = nullptr;
+    // prediction on active halo tiles: changed cells, per-cell linear
+    // extrapolation and prediction (tile layout), tile flags / list / slots
+    uint8_t *chg = nullptr;
+    float *pcell = nullptr, *predc = nullptr;
+    int *tflag = nullptr, *tlist = nullptr, *tslot = nullptr, *tcount = nullptr;
+    int tcap = 0;
     int l1 = 0;   // training loss: 0 mean squared error, 1 mean absolute error
     float h_norm[8] = {0, 1, 0, 1, 1, 1, 1, 1};
 };
@@ -735,9 +883,10 @@ cudaError_t salloc(swe_surrogate *s, void **p, size_t bytes) {
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
 
+// T: the images' side (the training tiles, or the halo tiles of prediction)
 template <int CIN, int NOUT, int EPI>
 cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, const __nv_bfloat16 *Wt, const float *bias,
-                 const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B) {
+                 const __nv_bfloat16 *mask, __nv_bfloat16 *Y, float *Yf, int B, int T) {
     (void)l;
     using WC = WsConv<CIN, NOUT>;
     auto kern = conv3x3_ws<CIN, NOUT, EPI>;
@@ -760,11 +909,11 @@ cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, con
     }
     // one wave: the column bands x images share the resident CTAs, each CTA
     // streams a run of rows (a multiple of 4, at least 8, to amortise its set-up)
-    const int bands = (s->T + 127) / 128;
+    const int bands = (T + 127) / 128;
     const int groups = std::max(1, resident / (bands * B));
-    const int rows = std::max(8, ((s->T + groups - 1) / groups + 3) / 4 * 4);
-    dim3 grid(bands, (s->T + rows - 1) / rows, B);
-    kern<<<grid, 192, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, s->T, s->T, rows, s->err);
+    const int rows = std::max(8, ((T + groups - 1) / groups + 3) / 4 * 4);
+    dim3 grid(bands, (T + rows - 1) / rows, B);
+    kern<<<grid, 192, smem, s->stream>>>(X, Wt, bias, mask, Y, Yf, T, T, rows, s->err);
     return cudaGetLastError();
 }
 
@@ -788,13 +937,14 @@ cudaError_t prep(swe_surrogate *s, NnLayer &l) {
     return cudaGetLastError();
 }
 
-cudaError_t forward_all(swe_surrogate *s, const __nv_bfloat16 *X, float *out, int B) {
-    cudaError_t e = conv<8, 32, EPI_RELU>(s, X, s->L[0], s->L[0].Wf, s->L[0].bias, nullptr, s->A[0], nullptr, B);
+cudaError_t forward_all(swe_surrogate *s, const __nv_bfloat16 *X, float *out, int B, int T) {
+    cudaError_t e = conv<8, 32, EPI_RELU>(s, X, s->L[0], s->L[0].Wf, s->L[0].bias, nullptr, s->A[0], nullptr, B, T);
     for (int i = 1; i < 5 && e == cudaSuccess; ++i)
-        e = conv<32, 32, EPI_RELU>(s, s->A[i - 1], s->L[i], s->L[i].Wf, s->L[i].bias, nullptr, s->A[i], nullptr, B);
-    if (e == cudaSuccess) e = conv<32, 16, EPI_OUT>(s, s->A[4], s->L[5], s->L[5].Wf, s->L[5].bias, X, nullptr, out, B);
+        e = conv<32, 32, EPI_RELU>(s, s->A[i - 1], s->L[i], s->L[i].Wf, s->L[i].bias, nullptr, s->A[i], nullptr, B, T);
+    if (e == cudaSuccess) e = conv<32, 16, EPI_OUT>(s, s->A[4], s->L[5], s->L[5].Wf, s->L[5].bias, X, nullptr, out, B, T);
     return e;
 }
+cudaError_t forward_all(swe_surrogate *s, const __nv_bfloat16 *X, float *out, int B) { return forward_all(s, X, out, B, s->T); }
 
 swe_status check_err(swe_surrogate *s) {
     int h = 0;
@@ -923,9 +1073,9 @@ extern "C" swe_status swe_surrogate_train_step(swe_surrogate *s, const void *Xv,
         e = cudaGetLastError();
     }
     // backward: gradient w.r.t. the pre-activations of layers 5..1, then weights
-    if (e == cudaSuccess) e = conv<8, 32, EPI_MASK>(s, s->dOut, s->L[5], s->L[5].Wd, nullptr, s->A[4], s->dA[4], nullptr, B);
+    if (e == cudaSuccess) e = conv<8, 32, EPI_MASK>(s, s->dOut, s->L[5], s->L[5].Wd, nullptr, s->A[4], s->dA[4], nullptr, B, s->T);
     for (int i = 4; i >= 1 && e == cudaSuccess; --i)
-        e = conv<32, 32, EPI_MASK>(s, s->dA[i], s->L[i], s->L[i].Wd, nullptr, s->A[i - 1], s->dA[i - 1], nullptr, B);
+        e = conv<32, 32, EPI_MASK>(s, s->dA[i], s->L[i], s->L[i].Wd, nullptr, s->A[i - 1], s->dA[i - 1], nullptr, B, s->T);
     if (e == cudaSuccess) e = wgrad<32, 16, 8>(s, s->A[4], s->dOut, s->L[5], B);
     for (int i = 4; i >= 1 && e == cudaSuccess; --i) e = wgrad<32, 32, 32>(s, s->A[i - 1], s->dA[i], s->L[i], B);
     if (e == cudaSuccess) e = wgrad<8, 32, 32>(s, X, s->dA[0], s->L[0], B);
@@ -1013,9 +1163,9 @@ __global__ void make_target(const float *__restrict__ b0, const float *__restric
 
 // Judged-window error sums (FP64) over the cells of the domain, ch = b1 - b0
 // the plain solver's bed change:  |pred - ch|, |ch|, |b1|, |last - ch|,
-// |p - ch| (p: input channel 6, the linear extrapolation).
+// |p - ch| (p: the linear extrapolation as the network reads it).
 __global__ void judge_sums(const float *__restrict__ b0, const float *__restrict__ b1, const float *__restrict__ pred,
-                           const float *__restrict__ last, const __nv_bfloat16 *__restrict__ X,
+                           const float *__restrict__ last, const float *__restrict__ pcell,
                            const float *__restrict__ norm, int nx, int ny, int T, int ntx, size_t total,
                            double *__restrict__ out) {
     __shared__ double red[5][256];
@@ -1030,7 +1180,7 @@ __global__ void judge_sums(const float *__restrict__ b0, const float *__restrict
         q[1] += fabs(ch);
         q[2] += fabs((double)b1[i]);
         q[3] += fabs((double)last[i] - ch);
-        q[4] += fabs((double)__bfloat162float(X[i * 8 + 6]) * norm[6] - ch);
+        q[4] += fabs((double)pcell[i] * norm[6] - ch);
     }
     for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = q[k];
     __syncthreads();
@@ -1092,12 +1242,58 @@ void launch_pack(swe_surrogate *s, const Coupling &k, __nv_bfloat16 *X) {
                                                        k.c->eps_f, k.c->f.ksh, s->bsave, s->act, X, k.total);
 }
 
-// Sets the bed to saved + prediction (s->out) and lets the handle re-form
+// The network's prediction for every cell of the coupled domain into
+// s->predc (tile layout), from the bed saved by launch_save and the current
+// state: the activity mask, the list of active halo tiles, and the network
+// on those tiles only, in batches that fit the activation buffers.
+swe_status predict_tiles(swe_surrogate *s, const Coupling &k) {
+    using namespace swe_nn;
+    const int nx = k.c->nx, ny = k.c->ny;
+    const size_t n = (size_t)nx * ny;
+    const int ntcx = (nx + kTC - 1) / kTC, ntcy = (ny + kTC - 1) / kTC, nt = ntcx * ntcy;
+    if (!s->chg) {
+        const size_t pix = (size_t)s->maxB * s->T * s->T;
+        if (salloc(s, (void **)&s->chg, pix) != cudaSuccess || salloc(s, (void **)&s->pcell, pix * 4) != cudaSuccess ||
+            salloc(s, (void **)&s->predc, pix * 4) != cudaSuccess || salloc(s, (void **)&s->tcount, 16) != cudaSuccess)
+            return SWE_ENOMEM;
+    }
+    if (nt > s->tcap) {
+        const int cap = std::max(nt, 64);
+        if (salloc(s, (void **)&s->tflag, (size_t)cap * 4) != cudaSuccess ||
+            salloc(s, (void **)&s->tlist, (size_t)cap * 4) != cudaSuccess ||
+            salloc(s, (void **)&s->tslot, (size_t)cap * 4) != cudaSuccess)
+            return SWE_ENOMEM;
+        s->tcap = cap;
+    }
+    const float4 *st = (const float4 *)k.cur;
+    bed_change<<<grid_n(n), 256, 0, s->stream>>>(st, nx, ny, s->T, k.ntx, s->bsave, s->norm, s->chg, s->pcell);
+    act_rows_rm<<<grid_n(n), 256, 0, s->stream>>>(s->chg, nx, ny, s->act);
+    tile_flags<<<grid_n(n), 256, 0, s->stream>>>(s->act, nx, ny, ntcx, ntcy, s->tflag);
+    compact_tiles<<<1, 1024, 0, s->stream>>>(s->tflag, nt, s->tlist, s->tslot, s->tcount);
+    int count = 0;
+    if (cudaMemcpyAsync(&count, s->tcount, 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return SWE_ECUDA;
+    const int cap = (int)(((size_t)s->maxB * s->T * s->T) / ((size_t)kTI * kTI));
+    for (int first = 0; first == 0 || first < count; first += cap) {
+        const int nimg = std::min(cap, count - first);
+        if (nimg > 0) {
+            gather_tiles<<<grid_n((size_t)nimg * kTI * kTI), 256, 0, s->stream>>>(
+                st, nx, ny, s->T, k.ntx, s->norm, k.c->eps_f, k.c->f.ksh, s->pcell, s->act, s->tlist, first, nimg, ntcx, s->X0);
+            if (forward_all(s, s->X0, s->out, nimg, kTI) != cudaSuccess) return SWE_ECUDA;
+        }
+        scatter_pred<<<grid_n(n), 256, 0, s->stream>>>(nx, ny, s->T, k.ntx, s->out, s->tslot, ntcx, first, nimg, s->predc);
+    }
+    return cudaGetLastError() == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
+// Sets the bed to saved + prediction (s->predc) and lets the handle re-form
 // its census and dt for the new bed.
 swe_status launch_apply(swe_surrogate *s, swe_handle *h, const Coupling &k) {
-    apply_bed<<<grid_n(k.total), 256, 0, s->stream>>>((float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->out, s->bsave,
+    apply_bed<<<grid_n(k.total), 256, 0, s->stream>>>((float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->predc, s->bsave,
                                                       s->norm, k.total);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) return SWE_ECUDA;
+    const swe_status r = before_solver(s, k);
+    if (r != SWE_OK) return r;
     return (swe_status)swe_impl::handle_state_changed(h);
 }
 }  // namespace
@@ -1136,9 +1332,7 @@ extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
     if (!couple(s, h, k)) return SWE_EINVAL;
     swe_status st = after_solver(s, k);
     if (st != SWE_OK) return st;
-    launch_pack(s, k, s->X0);
-    if (forward_all(s, s->X0, s->out, k.ntx * k.nty) != cudaSuccess) return SWE_ECUDA;
-    if ((st = check_err(s)) != SWE_OK) return st;
+    if ((st = predict_tiles(s, k)) != SWE_OK || (st = check_err(s)) != SWE_OK) return st;
     return launch_apply(s, h, k);
 }
 
@@ -1147,7 +1341,6 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
     Coupling k;
     if (!st || nwindows < 0 || K < 2 || f < 1 || (K % f) || judge_every < 1 || !(bound > 0) || !couple(s, h, k))
         return SWE_EINVAL;
-    const int B = k.ntx * k.nty;
     double *dsum = nullptr;
     float *last = nullptr;
     if (cudaMalloc(&dsum, 5 * sizeof(double)) != cudaSuccess) return SWE_ENOMEM;
@@ -1162,13 +1355,14 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
         launch_save(s, k, s->bsave);
         if ((r = before_solver(s, k)) != SWE_OK || (r = swe_run_steps(h, 1)) != SWE_OK) return r;
         if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
-        launch_pack(s, k, s->X0);
-        if (forward_all(s, s->X0, s->out, B) != cudaSuccess) return SWE_ECUDA;
+        if ((r = predict_tiles(s, k)) != SWE_OK) return r;
         return before_solver(s, k);   // the forward's error flag is read once per window
     };
+    double t_next = 0;   // the time at the start of the next window (read once; each window ends by reading it)
+    if (nwindows > 0) rc = swe_get_time(h, &t_next);
     for (int w = 0; w < nwindows && rc == SWE_OK; ++w) {
-        double t0 = 0, t1 = 0;
-        if ((rc = swe_get_time(h, &t0)) != SWE_OK) break;
+        const double t0 = t_next;
+        double t1 = 0;
         if (st->mode == 1) {                                     // plain coupled window
             if ((rc = swe_run_steps(h, K)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
             st->bed_time += t1 - t0;
@@ -1181,8 +1375,8 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             if ((rc = check_err(s)) != SWE_OK) break;
             launch_save(s, k, s->tgt);
             cudaMemsetAsync(dsum, 0, 5 * sizeof(double), s->stream);
-            judge_sums<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->out, last, s->X0, s->norm, k.c->nx,
-                                                              k.c->ny, s->T, k.ntx, k.total, dsum);
+            judge_sums<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, s->predc, last, s->pcell, s->norm,
+                                                              k.c->nx, k.c->ny, s->T, k.ntx, k.total, dsum);
             diff_into<<<grid_n(k.total), 256, 0, s->stream>>>(s->bsave, s->tgt, last, k.total);
             double q[5];
             if (cudaMemcpyAsync(q, dsum, sizeof q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
@@ -1217,6 +1411,7 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             ++st->surrogate_windows;
         }
         ++st->windows;
+        t_next = t1;
     }
     cudaStreamSynchronize(s->stream);
     cudaFree(dsum);
