@@ -325,7 +325,13 @@ swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, in
 swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h);
 swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target);
 /* Predicts the window's bed change from the handle's current state and sets
- * the bed to the saved bed plus that change. */
+ * the bed to the saved bed plus that change.  The network runs only on the
+ * halo tiles (116 x 116 interior cells plus a 6-cell margin, as 128 x 128
+ * images) that hold a cell of the activity mask; elsewhere the prediction is
+ * exactly 0.  Device work of a few kernels and one host sync for the tile
+ * count.  Errors: SWE_EINVAL (handle not FP32, state not set, or domain
+ * larger than max_batch tiles), SWE_ENOMEM (first call's scratch), SWE_ECUDA,
+ * SWE_ETIMEOUT (a convolution's bounded wait gave up). */
 swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h);
 /* Runs nwindows windows, each worth K coupled steps of bed evolution.  A
  * surrogate window saves the bed, runs one coupled step, predicts the
