@@ -684,11 +684,16 @@ __global__ void apply_bed(float4 *__restrict__ state, int nx, int ny, int T, int
 // neighbourhood.  The domain is cut into interior tiles of kTC x kTC cells;
 // the network runs only on the tiles whose activity mask holds a 1 (where it
 // is all zero the output m (z + bias + p) is exactly 0), each as a kTI x kTI
-// image of the interior and a kHalo-cell margin from its neighbours (zeros
-// beyond the domain, as for the whole-domain images).
+// image of the interior and a kHalo-cell margin from its neighbours.  An
+// image never reaches beyond the domain: at the domain's edges it is shifted
+// inwards, so its own edge (where every layer pads with zeros) is the
+// domain's, as in a whole-domain image (domains of at least kTI x kTI).
 constexpr int kTI = 128;
 constexpr int kHalo = 6;
 constexpr int kTC = kTI - 2 * kHalo;
+
+// first row / column of the image of interior tile t along an axis of n cells
+__device__ __forceinline__ int halo_origin(int t, int n) { return min(max(t * kTC - kHalo, 0), n - kTI); }
 
 // chg: 1 where the bed differs from the saved bed (row-major); pcell: the
 // linear extrapolation (b - b_saved) / norm[7] rounded to BF16 as the network
@@ -773,10 +778,10 @@ __global__ void gather_tiles(const float4 *__restrict__ state, int nx, int ny, i
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / (kTI * kTI)), r = (int)(i % (kTI * kTI));
         const int tile = list[first + b];
-        const int y = (tile / ntcx) * kTC - kHalo + r / kTI, x = (tile % ntcx) * kTC - kHalo + r % kTI;
+        const int y = halo_origin(tile / ntcx, ny) + r / kTI, x = halo_origin(tile % ntcx, nx) + r % kTI;
         __align__(16) __nv_bfloat16 o[8];
         float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (x >= 0 && y >= 0 && x < nx && y < ny) {
+        {
             const float4 c = state[(size_t)y * nx + x];
             f[0] = (c.x - norm[0]) / norm[1];
             f[1] = (c.w - norm[2]) / norm[3];
@@ -813,7 +818,7 @@ __global__ void scatter_pred(int nx, int ny, int T, int ntx, const float *__rest
             v = 0.f;
         } else {
             if (sl < first || sl >= first + nimg) continue;
-            v = out[((size_t)(sl - first) * kTI + (y - ty * kTC + kHalo)) * kTI + (x - tx * kTC + kHalo)];
+            v = out[((size_t)(sl - first) * kTI + (y - halo_origin(ty, ny))) * kTI + (x - halo_origin(tx, nx))];
         }
         predc[tile_index(x, y, T, ntx)] = v;
     }
@@ -1267,6 +1272,12 @@ swe_status predict_tiles(swe_surrogate *s, const Coupling &k) {
     }
     const float4 *st = (const float4 *)k.cur;
     bed_change<<<grid_n(n), 256, 0, s->stream>>>(st, nx, ny, s->T, k.ntx, s->bsave, s->norm, s->chg, s->pcell);
+    if (nx < kTI || ny < kTI) {   // smaller than one halo image: the network on the whole-domain tiles
+        launch_pack(s, k, s->X0);
+        if (forward_all(s, s->X0, s->out, k.ntx * k.nty) != cudaSuccess) return SWE_ECUDA;
+        return cudaMemcpyAsync(s->predc, s->out, k.total * 4, cudaMemcpyDeviceToDevice, s->stream) == cudaSuccess
+                   ? SWE_OK : SWE_ECUDA;
+    }
     act_rows_rm<<<grid_n(n), 256, 0, s->stream>>>(s->chg, nx, ny, s->act);
     tile_flags<<<grid_n(n), 256, 0, s->stream>>>(s->act, nx, ny, ntcx, ntcy, s->tflag);
     compact_tiles<<<1, 1024, 0, s->stream>>>(s->tflag, nt, s->tlist, s->tslot, s->tcount);

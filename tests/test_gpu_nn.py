@@ -184,3 +184,47 @@ def test_surrogate_windows_advance_the_bed_faster(lib):
     want = (b0 + p * 1e-3).astype(np.float32)
     assert np.allclose(got, want, rtol=0, atol=1e-6 * max(1.0, np.abs(b0).max()))
     S.close()
+
+
+def test_surrogate_halo_tiles_match_the_whole_domain_network(lib):
+    """The prediction of the surrogate windows runs the network only on the
+    116^2 interior tiles that hold a cell of the activity mask, each as a
+    128^2 image with a 6-cell margin (the receptive field of six 3x3
+    layers).  On a 256^2 domain (ragged tiles) it must equal the same network
+    run on the whole domain as one 256^2 image, cell by cell, with every
+    inactive tile exactly unchanged."""
+    import torch
+    from oracle import cnn_oracle as C
+    from paper_2103_15196_gb300 import inputs as I
+    from paper_2103_15196_gb300 import swe
+    sc, Sv = _solver_case(swe, I)
+    n, K = 256, 50
+    S = swe.Surrogate(tile=n, max_batch=1, seed=5)
+    for i, (Wm, b) in enumerate(C.random_params(5)):
+        S.set_params(i, Wm, b)
+    H, _, _, b0 = Sv.get_state(np.float32)
+    S.set_norm([float(H.mean()), float(H.std()) + 1e-6, float(b0.mean()), float(b0.std()) + 1e-6, 1.0, 1.0,
+                1e-3, 1e-3 / K])
+    S.save_bed(Sv)
+    Sv.run_steps(1)
+    X = torch.empty((1, n, n, 8), dtype=torch.bfloat16, device="cuda")
+    assert S.pack_state(Sv, X) == 1
+    out = torch.zeros((1, n, n), dtype=torch.float32, device="cuda")
+    S.forward(X, out, 1)
+    torch.cuda.synchronize()
+    pred = out[0].cpu().numpy().astype(np.float64)
+    mask = X[0, :, :, 7].float().cpu().numpy() > 0
+    S.apply(Sv)
+    got = Sv.get_state(np.float32)[3].astype(np.float64)
+    want = b0.astype(np.float64) + pred * 1e-3
+    assert np.abs(got - want).max() <= 2e-6 * max(1.0, np.abs(b0).max())
+    # both branches are exercised: some interior tiles active, some not
+    tiles = [(ty, tx) for ty in range(3) for tx in range(3)]
+    act = [mask[ty * 116:(ty + 1) * 116, tx * 116:(tx + 1) * 116].any() for ty, tx in tiles]
+    print("active interior tiles", act, "mask cells", int(mask.sum()))
+    assert any(act) and not all(act), act
+    for (ty, tx), a in zip(tiles, act):
+        if not a:
+            sl = (slice(ty * 116, (ty + 1) * 116), slice(tx * 116, (tx + 1) * 116))
+            assert np.array_equal(got[sl], b0.astype(np.float64)[sl])
+    S.close()
