@@ -78,18 +78,29 @@ __device__ bool grid_sync(unsigned *bar, unsigned expected, unsigned long long t
 template <int BW, bool GEN>
 __global__ void __launch_bounds__(BW, 2)
 ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restrict__ items, int nitems,
-                int nsteps, unsigned *bar, unsigned expected, unsigned *status, unsigned long long timeout_ns) {
+                int nsteps, unsigned *bar, unsigned expected, unsigned *status, unsigned long long timeout_ns,
+                unsigned *ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
+    __shared__ int s_it;
     for (int step = 0; step < nsteps; ++step) {
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-            const int4 w = items[it];
+        // work items taken in order from a counter (ctr[step parity], zero at
+        // the step's start): a block that drew cheap (dry) items takes more
+        for (;;) {
             __syncthreads();
+            if (threadIdx.x == 0) s_it = (int)atomicAdd(ctr + (step & 1), 1u);
+            __syncthreads();
+            const int it = s_it;
+            if (it >= nitems) break;
+            const int4 w = items[it];
             step_tile<float, BW, true, true, GEN>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
         }
         if (!grid_sync(bar, expected, timeout_ns, status)) return;
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (int k = threadIdx.x; k < nscen; k += BW) between_body<float>(scen[k].c, scen[k].B, 1);
+            // the next step's counter: its last use ended before the barrier above
+            if (threadIdx.x == 0) atomicExch(ctr + ((step + 1) & 1), 0u);
+        }
         if (!grid_sync(bar, expected, timeout_ns, status)) return;
     }
 }
@@ -104,7 +115,7 @@ struct swe_ensemble {
     EnsScen *d_scen = nullptr;
     int4 *d_items = nullptr;
     size_t items_cap = 0;
-    unsigned *d_bar = nullptr;   // [0] arrivals, [1] generation, [2] status
+    unsigned *d_bar = nullptr;   // [0] arrivals, [1] generation, [2] status, [3..4] work counters
     unsigned long long timeout_ns = 2000000000ull;
     int extra_arrivals = 0;
     std::map<long long, cudaGraphExec_t> graphs;
@@ -169,6 +180,7 @@ template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int n
     const int grid = e->grid;
     const size_t smem = sizeof(StepSmem<float, BW>);
     cudaError_t err = cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned), e->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(e->d_bar + 3, 0, 2 * sizeof(unsigned), e->stream);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -183,7 +195,8 @@ template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int n
     const EnsScen *sc = e->d_scen;
     const int4 *it = e->d_items;
     return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN>, sc, (int)e->members.size(), it, e->nitems, nsteps,
-                              e->d_bar, (unsigned)(grid + e->extra_arrivals), e->d_bar + 2, e->timeout_ns);
+                              e->d_bar, (unsigned)(grid + e->extra_arrivals), e->d_bar + 2, e->timeout_ns,
+                              e->d_bar + 3);
 }
 
 cudaError_t launch_any(swe_ensemble *e, int nsteps) {
@@ -220,7 +233,7 @@ swe_status check(swe_ensemble *e) {
         return SWE_ECUDA;
     if (st & SWE_STATUS_TIMEOUT) {
         // clear the bit so the ensemble can be used again once the cause is fixed
-        cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream);
+        cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream);
         cudaStreamSynchronize(e->stream);
         return SWE_ETIMEOUT;
     }
@@ -260,8 +273,8 @@ extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void 
         e->members.push_back(h);
     }
     if (cudaMalloc(&e->d_scen, n * sizeof(EnsScen)) != cudaSuccess ||
-        cudaMalloc(&e->d_bar, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream) != cudaSuccess) {
+        cudaMalloc(&e->d_bar, 8 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream) != cudaSuccess) {
         swe_ensemble_destroy(e);
         return SWE_ENOMEM;
     }
@@ -315,7 +328,7 @@ extern "C" swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, 
     e->timeout_ns = (unsigned long long)(seconds * 1e9);
     e->extra_arrivals = extra_arrivals;
     clear_graphs(e);
-    if (cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned), e->stream) != cudaSuccess) return SWE_ECUDA;
+    if (cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream) != cudaSuccess) return SWE_ECUDA;
     return SWE_OK;
 }
 
