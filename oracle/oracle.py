@@ -123,6 +123,8 @@ def lib():
         L.orc_census.argtypes = [ctypes.POINTER(_Params), dp, u8, ctypes.POINTER(ctypes.c_int)]
         L.orc_hll.restype = ctypes.c_double
         L.orc_hll.argtypes = [ctypes.c_double] * 6
+        L.orc_minmod.restype = ctypes.c_double
+        L.orc_minmod.argtypes = [ctypes.c_double] * 2
         L.orc_hydro_integral.restype = ctypes.c_double
         L.orc_hydro_integral.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double]
         L.orc_num_threads.restype = ctypes.c_int
@@ -272,6 +274,10 @@ def census(p: Params, H, src=None):
 
 def hll(UL, UR, FL, FR, sL, sR):
     return lib().orc_hll(UL, UR, FL, FR, sL, sR)
+
+
+def minmod(a, b):
+    return lib().orc_minmod(a, b)
 
 
 def run(p: Params, st: State, n, nsteps: int, src=None, qb=None, hydro=None, t: float = 0.0,

@@ -111,6 +111,9 @@ static double minmod(double a, double b)
     return 0.0;
 }
 
+/* The limiter, exported for its unit test. */
+double orc_minmod(double a, double b) { return minmod(a, b); }
+
 /* HLL flux of a scalar advected with speed s between left and right states.
  * sL = min(uL, uR), sR = max(uL, uR) for the advective (pressure-free) flux of
  * Eq. 6; the pressure and bed-slope terms live in the source Phi. */

@@ -41,6 +41,27 @@ def test_hll_textbook_identities(orc):
     assert h(0.0, 3.0, 1.0, 4.0, -1.0, 2.0) == pytest.approx(0.0, abs=1e-15)
 
 
+def test_minmod_is_the_median_with_zero(orc):
+    """The limiter of the K7 reconstruction: minmod(a, b) is 0 when the two
+    slopes differ in sign (or one is 0) and the one of smaller magnitude
+    otherwise; equivalently the median of (a, b, 0).  Checked on the
+    textbook cases and against that characterisation on random pairs
+    spanning signs, ties and magnitudes."""
+    m = orc.minmod
+    assert m(1.0, 2.0) == 1.0 and m(2.0, 1.0) == 1.0
+    assert m(-1.0, -2.0) == -1.0 and m(-2.0, -1.0) == -1.0
+    assert m(1.0, -2.0) == 0.0 and m(-1.0, 2.0) == 0.0
+    assert m(0.0, 3.0) == 0.0 and m(3.0, 0.0) == 0.0
+    assert m(0.75, 0.75) == 0.75 and m(-0.75, -0.75) == -0.75
+    rng = np.random.default_rng(17)
+    a = rng.normal(size=2000) * 10.0 ** rng.integers(-6, 4, size=2000)
+    b = rng.normal(size=2000) * 10.0 ** rng.integers(-6, 4, size=2000)
+    b[::7] = a[::7]
+    b[::11] = -a[::11]
+    for x, y in zip(a, b):
+        assert m(x, y) == float(np.median([x, y, 0.0]))
+
+
 def test_hydrograph_integral_closed_form(orc):
     """Area under the triangular hydrograph 0 -> 500 (t=1200) -> 0 (t=3600)."""
     hg = orc.Hydrograph([0.0, 1200.0, 3600.0], [0.0, 500.0, 0.0])
