@@ -839,6 +839,7 @@ __global__ void scatter_pred(int nx, int ny, int T, int ntx, const float *__rest
 #include <vector>
 
 #include "swe_internal.h"
+#include "swe_trace.h"
 
 namespace {
 
@@ -1061,6 +1062,7 @@ extern "C" swe_status swe_surrogate_set_loss(swe_surrogate *s, int kind) {
 }
 
 extern "C" swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, float *out, int B) {
+    const SweRange range_("swe_surrogate_forward");
     if (!s || !X || !out || B < 1 || B > s->maxB) return SWE_EINVAL;
     if (forward_all(s, (const __nv_bfloat16 *)X, out, B) != cudaSuccess) return SWE_ECUDA;
     return check_err(s);
@@ -1068,6 +1070,7 @@ extern "C" swe_status swe_surrogate_forward(swe_surrogate *s, const void *X, flo
 
 extern "C" swe_status swe_surrogate_train_step(swe_surrogate *s, const void *Xv, const float *target, int B, float lr,
                                               float *loss_out) {
+    const SweRange range_("swe_surrogate_train_step");
     if (!s || !Xv || !target || B < 1 || B > s->maxB || !(lr > 0)) return SWE_EINVAL;
     const __nv_bfloat16 *X = (const __nv_bfloat16 *)Xv;
     const size_t pix = (size_t)B * s->T * s->T;
@@ -1339,6 +1342,7 @@ extern "C" swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h,
 }
 
 extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
+    const SweRange range_("swe_surrogate_apply");
     Coupling k;
     if (!couple(s, h, k)) return SWE_EINVAL;
     swe_status st = after_solver(s, k);
@@ -1349,6 +1353,7 @@ extern "C" swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h) {
 
 extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwindows, int K, int f, int judge_every,
                                        double bound, swe_surrogate_stats *st) {
+    const SweRange range_("swe_surrogate_run");
     Coupling k;
     if (!st || nwindows < 0 || K < 2 || f < 1 || (K % f) || judge_every < 1 || !(bound > 0) || !couple(s, h, k))
         return SWE_EINVAL;
@@ -1372,6 +1377,7 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
     double t_next = 0;   // the time at the start of the next window (read once; each window ends by reading it)
     if (nwindows > 0) rc = swe_get_time(h, &t_next);
     for (int w = 0; w < nwindows && rc == SWE_OK; ++w) {
+        const SweRange window_(st->mode == 1 ? "plain window" : (w % judge_every == 0 ? "judged window" : "surrogate window"));
         const double t0 = t_next;
         double t1 = 0;
         if (st->mode == 1) {                                     // plain coupled window

@@ -11,6 +11,7 @@
 
 #include "../../include/swe.h"
 #include "swe_internal.h"
+#include "swe_trace.h"
 
 using namespace swe_impl;
 
@@ -405,6 +406,7 @@ static swe_status check_status(swe_handle *h) {
 
 extern "C" swe_status swe_set_state_ex(swe_handle *h, const void *H, const void *Hu, const void *Hv, const void *bb,
                                        int dtype, int where) {
+    const SweRange range_("swe_set_state");
     if (!h || !H || !Hu || !Hv || !bb || (dtype != SWE_FP64 && dtype != SWE_FP32) ||
         (where != SWE_HOST && where != SWE_DEVICE))
         return fail(h, SWE_EINVAL, "swe_set_state: bad argument");
@@ -443,6 +445,7 @@ extern "C" swe_status swe_set_state(swe_handle *h, const double *H, const double
 }
 
 extern "C" swe_status swe_get_state_ex(swe_handle *h, void *H, void *Hu, void *Hv, void *bb, int dtype, int where) {
+    const SweRange range_("swe_get_state");
     if (!h || (dtype != SWE_FP64 && dtype != SWE_FP32) || (where != SWE_HOST && where != SWE_DEVICE))
         return fail(h, SWE_EINVAL, "swe_get_state: bad argument");
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_get_state before swe_set_state");
@@ -508,6 +511,7 @@ static swe_status ensure_graph(swe_handle *h) {
 }
 
 extern "C" swe_status swe_step(swe_handle *h, double *dt_taken) {
+    const SweRange range_("swe_step");
     if (!h) return SWE_EINVAL;
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_step before swe_set_state");
     swe_status s = free_stepping(h);
@@ -520,6 +524,7 @@ extern "C" swe_status swe_step(swe_handle *h, double *dt_taken) {
 }
 
 extern "C" swe_status swe_run_steps(swe_handle *h, int64_t nsteps) {
+    const SweRange range_("swe_run_steps");
     if (!h || nsteps < 0) return fail(h, SWE_EINVAL, "swe_run_steps: bad argument");
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_run_steps before swe_set_state");
     swe_status s = free_stepping(h);
@@ -536,6 +541,7 @@ extern "C" swe_status swe_run_steps(swe_handle *h, int64_t nsteps) {
 }
 
 extern "C" swe_status swe_advance(swe_handle *h, double t_end, int64_t *steps_taken) {
+    const SweRange range_("swe_advance");
     if (!h || !std::isfinite(t_end)) return fail(h, SWE_EINVAL, "swe_advance: bad argument");
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_advance before swe_set_state");
     swe_status s = read_dev(h);

@@ -22,6 +22,7 @@
 
 #include "../../include/swe.h"
 #include "swe_kernels.cuh"
+#include "swe_trace.h"
 
 using namespace swe_impl;
 
@@ -302,6 +303,7 @@ extern "C" swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **m
 }
 
 extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
+    const SweRange range_("swe_ensemble_run");
     if (!e || nsteps < 0) return SWE_EINVAL;
     if (nsteps == 0) return SWE_OK;
     swe_status s = upload(e);

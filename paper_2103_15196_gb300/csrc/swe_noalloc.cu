@@ -30,6 +30,7 @@
 
 #include "../../include/swe.h"
 #include "swe_internal.h"
+#include "swe_trace.h"
 
 using namespace swe_impl;
 
@@ -71,6 +72,7 @@ swe_status scratch_address(void **out) {
 
 extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, const void *state_in,
                                        void *state_out, void *cuda_stream, double *dt_taken) {
+    const SweRange range_("swe_step_noalloc");
     if (!pp || !state_in || !state_out || state_in == state_out) return err(SWE_EINVAL, "bad pointer argument");
     const swe_params &p = *pp;
     if ((reinterpret_cast<uintptr_t>(state_in) | reinterpret_cast<uintptr_t>(state_out)) & 15u)
