@@ -96,7 +96,8 @@ typedef struct {
     int32_t active_tiles;   /* blocks computed in the last step (HGS) */
     int32_t total_tiles;    /* blocks per step */
     int32_t tile_x, tile_y; /* HGS block size in cells */
-    uint32_t status;        /* device status bits: 1 non-finite, 2 negative depth */
+    uint32_t status;        /* device status bits: 1 non-finite, 2 negative depth,
+                               8 an index outside its buffer (checked build only) */
     uint64_t cells_computed;/* cells of computed blocks, summed over steps since set_state */
     uint64_t cells_copied;  /* cells of skipped blocks that were copied, summed likewise */
 } swe_diag;

@@ -17,6 +17,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libswe.so")
+# the checked variant (-DSWE_CHECKED): every global index of the step kernel
+# is tested against its buffer; built on demand by the tests
+LIB_CHECKED = os.path.join(OUT_DIR, "libswe_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,21 +46,24 @@ def _sources():
            [os.path.join(INCLUDE, "swe.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(checked):
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
+    extra = list(extra) + (["-DSWE_CHECKED"] if checked else [])
 
     def compile_one(name):
-        obj = os.path.join(OUT_DIR, name.replace(".cu", ".o"))
+        obj = os.path.join(OUT_DIR, name.replace(".cu", "_checked.o" if checked else ".o"))
         cmd = [cc, "-c", os.path.join(SRC, name), "-o", obj] + COMMON + UNITS[name] + list(extra)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,12 +74,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

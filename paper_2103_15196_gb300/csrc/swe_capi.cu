@@ -397,8 +397,10 @@ static swe_status read_dev(swe_handle *h) {
 static swe_status check_status(swe_handle *h) {
     if (h->h_dev->status) {
         char msg[128];
-        std::snprintf(msg, sizeof msg, "numerical failure (status 0x%x): %s", h->h_dev->status,
-                      (h->h_dev->status & 1u) ? "non-finite value" : "depth below -neg_tol");
+        const unsigned s = h->h_dev->status;
+        std::snprintf(msg, sizeof msg, "step failure (status 0x%x): %s", s,
+                      (s & 8u) ? "an index outside its buffer (checked build)"
+                               : ((s & 1u) ? "non-finite value" : "depth below -neg_tol"));
         return fail(h, SWE_ENUMERIC, msg);
     }
     return SWE_OK;

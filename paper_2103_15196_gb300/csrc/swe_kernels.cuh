@@ -38,6 +38,27 @@
 
 namespace swe_impl {
 
+// ------------------------------------------------------------ checked build
+//
+// Built with -DSWE_CHECKED (the library's checked variant, for tests), every
+// global access of the step kernel first tests its index against its buffer:
+// an index outside sets SWE_STATUS_BOUNDS in the device status word and the
+// access is skipped.  In the production build SWE_IN is the constant true.
+#define SWE_STATUS_BOUNDS 8u
+#ifdef SWE_CHECKED
+__device__ inline bool swe_in(long long i, long long n, SweDev *dev) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&dev->status, SWE_STATUS_BOUNDS);
+    return false;
+}
+#define SWE_IN(i, n) swe_in((long long)(i), (long long)(n), B.dev)
+#else
+#define SWE_IN(i, n) true
+#endif
+// cells of the grid, entries of the Manning tables
+#define SWE_NCELL ((long long)c.nx * c.ny)
+#define SWE_NMAN ((long long)((((c.ny - 1) >> c.man_shift) + 1) * c.man_w))
+
 // ------------------------------------------------------------ state cells
 
 template <typename T> struct CellIO;
@@ -140,6 +161,7 @@ __device__ inline int ext_index(int i, int n, int lo_open, int hi_open, int &sgn
             break;
         }
     }
+    if (i < 0 || i >= n) i = i < 0 ? 0 : n - 1;   // never outside the grid
     sgn = s;
     return i;
 }
@@ -493,7 +515,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             aH = bH; aHu = bHu; aHv = bHv; ab = bb0; asy = bsy;
             if (s + 2 <= y1 + 3) {
                 const int yy = reflect(s + 2, c.ny, c.bc[2], c.bc[3], bsy);
-                load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
+                if (SWE_IN((long long)yy * c.nx + xx, SWE_NCELL)) load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
             const bool wet = is_wet(H, c);
             HB<P, 0>()[o] = V2<T>{H, bb};
@@ -518,7 +540,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 const T bc = C.y, u = q4<P, 2>(S.u)[o], v = vB[P];
                 int sy;
                 const int my = reflect(r, c.ny, c.bc[2], c.bc[3], sy) >> c.man_shift;
-                if (my != gn2_row) {
+                if (my != gn2_row && SWE_IN(my * c.man_w + mcol, SWE_NMAN)) {
                     gn2_row = my;
                     gn2 = tab<T>(B.gn2, my * c.man_w + mcol);
                     if (GEN && c.aj_mode == 1) ajo = tab<T>(B.ajn, my * c.man_w + mcol);
@@ -560,16 +582,18 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             const V2<T> C = HB<P, 5>()[o];
             const T Hc = C.x, bc = C.y;
             bool src = false;
-            if (SRC && c.nsrc > 0)
-                for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q) src |= (B.src_x[q] == x);
+            if (SRC && c.nsrc > 0 && SWE_IN(r + 1, c.ny + 1))
+                for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q)
+                    if (SWE_IN(q, c.nsrc)) src |= (B.src_x[q] == x);
             const V4<T> f = S.xf[PM5_2][o], fw = S.xf[PM5_2][o - 1];
             const V2<T> w = q4<P, 5>(S.W)[o];
             T hn = Hc - k.dtdx * ((f.a - fw.a) + (G1[0] - G2[0]));
             if (src) hn = hn + k.dHs;
-            if (SRC && c.has_rain) hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
+            if (SRC && c.has_rain && SWE_IN((long long)r * c.nx + x, SWE_NCELL))
+                hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * w.x - k.dtdx * ((f.b - fw.b) + (G1[1] - G2[1]));
             T hvn = Hc * w.y - k.dtdx * ((f.c - fw.c) + (G1[2] - G2[2]));
-            if (SRC && c.has_beta) {
+            if (SRC && c.has_beta && SWE_IN((long long)r * c.nx + x, SWE_NCELL)) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
                 if (loss > hn) loss = hn > T(0) ? hn : T(0);
@@ -582,8 +606,8 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             }
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
             const T bn = bc - k.cb * ((f.d - fw.d) + (G1[3] - G2[3]));
-            CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
-            if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row) {
+            if (SWE_IN((long long)r * c.nx + x, SWE_NCELL)) CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
+            if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row && SWE_IN((r >> c.man_shift) * c.man_w + mcol, SWE_NMAN)) {
                 aj_row = r >> c.man_shift;
                 aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
             }
@@ -678,7 +702,8 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     if (c.hgs) {
         int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
         int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
-        auto cen = [&](int i) { return COHERENT ? __ldcg(cen_in + i) : cen_in[i]; };
+        const int nt = c.tiles_x * c.tiles_y;
+        auto cen = [&](int i) { return SWE_IN(i, nt) ? (COHERENT ? __ldcg(cen_in + i) : cen_in[i]) : 0; };
         bool active = cen(tile) > 0 || cen(by * c.tiles_x + l) > 0 || cen(by * c.tiles_x + r) > 0 ||
                       cen(d * c.tiles_x + bx) > 0 || cen(u * c.tiles_x + bx) > 0;
         if (!active) {
@@ -686,6 +711,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
                 int x1 = min(tx0 + c.tw, c.nx);
                 for (int y = y0; y < y1; ++y)
                     for (int x = tx0 + t; x < x1; x += BW) {
+                        if (!SWE_IN((long long)y * c.nx + x, SWE_NCELL)) continue;
                         if (COHERENT) CellIO<T>::copy_cg(in, out, (long long)y * c.nx + x);
                         else CellIO<T>::copy(in, out, (long long)y * c.nx + x);
                     }
@@ -707,7 +733,9 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     w.in = in; w.out = out; w.y0 = y0; w.y1 = y1;
     w.x = tx0 - 4 + t;                               // this thread's column
     int sx;
-    w.xx = reflect(w.x, c.nx, c.bc[0], c.bc[1], sx);
+    // columns more than 4 past the grid feed no output cell; clamped, their
+    // ghost index stays a few reflections away even on a 1-column grid
+    w.xx = reflect(min(w.x, c.nx + 3), c.nx, c.bc[0], c.bc[1], sx);
     w.sxT = T(sx);
     w.mcol = w.xx >> c.man_shift;
     w.out_lane = (t >= 4) && (t < BW - 4) && (w.x < c.nx);
@@ -722,9 +750,9 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
     {
         int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
-        w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
+        if (SWE_IN((long long)yy * c.nx + w.xx, SWE_NCELL)) w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
         yy = reflect(y0 - 3, c.ny, c.bc[2], c.bc[3], w.bsy);
-        w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
+        if (SWE_IN((long long)yy * c.nx + w.xx, SWE_NCELL)) w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
     }
     // sweep positions y0-8 .. y1+4 in pairs (y0 is a multiple of 8)
     for (int s = y0 - 8; s <= y1 + 4; s += 2) {
@@ -805,6 +833,7 @@ __global__ void __launch_bounds__(BW, sizeof(T) == 4 ? ((SRC || GEN) ? 2 : 3) : 
     const int i = blockIdx.x;
     if (i >= B.work[0]) return;
     const int tile = B.work[2 + i];
+    if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
     step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
 }
 

@@ -86,7 +86,7 @@ class SurrogateStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-_lib = None
+_libs = {False: None, True: None}
 
 
 def header_functions():
@@ -95,14 +95,15 @@ def header_functions():
     return sorted(set(re.findall(r"^\s*(?:swe_status|const char \*)\s*(swe_\w+)\s*\(", txt, re.M)))
 
 
-def load_library(build_if_missing: bool = True):
-    """Loads (building it first if needed) the in-tree CUDA library."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        path = _build.build()
+def load_library(build_if_missing: bool = True, checked: bool = False):
+    """Loads (building it first if needed) the in-tree CUDA library; checked:
+    its variant that tests every global index of the step kernel against its
+    buffer (device status bit 8 on a skipped access)."""
+    if _libs[checked] is not None:
+        return _libs[checked]
+    path = _build.LIB_CHECKED if checked else _build.LIB
+    if build_if_missing and not _build.up_to_date(checked):
+        path = _build.build(checked=checked)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
     L = ctypes.CDLL(path)
@@ -163,7 +164,7 @@ def load_library(build_if_missing: bool = True):
         f.restype = ctypes.c_int
     L.swe_last_error.argtypes = [H]
     L.swe_last_error.restype = ctypes.c_char_p
-    _lib = L
+    _libs[checked] = L
     return L
 
 
@@ -179,6 +180,8 @@ class Solver:
     """One CSPH-TVD + Exner grid on the current CUDA device.
 
     precision: 'fp32' (FP32 state, FP64 dt/accumulators) or 'fp64'.
+    checked: run on the library's checked variant (every global index of
+    the step kernel tested against its buffer; for tests).
     Other keyword arguments override fields of ``swe_params``."""
 
     @classmethod
@@ -193,8 +196,8 @@ class Solver:
         self._owned = False
         return self
 
-    def __init__(self, nx, ny, dx, precision="fp32", stream=None, **kw):
-        L = load_library()
+    def __init__(self, nx, ny, dx, precision="fp32", stream=None, checked=False, **kw):
+        L = load_library(checked=checked)
         self._L = L
         self._owned = True
         p = Params()
