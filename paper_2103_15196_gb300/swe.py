@@ -185,10 +185,10 @@ class Solver:
     Other keyword arguments override fields of ``swe_params``."""
 
     @classmethod
-    def _view(cls, handle, params, precision="fp32"):
+    def _view(cls, handle, params, precision="fp32", lib=None):
         """A non-owning view of a handle owned elsewhere (an ensemble member)."""
         self = cls.__new__(cls)
-        self._L = load_library()
+        self._L = lib if lib is not None else load_library()
         self.params = params
         self.nx, self.ny, self.dx = params.nx, params.ny, params.dx
         self.precision = precision
@@ -355,10 +355,11 @@ class Solver:
 class Ensemble:
     """Independent scenarios advanced together by one persistent launch per
     run call (swe_ensemble_* in include/swe.h).  specs: list of dicts with
-    nx, ny, dx and optional swe_params fields."""
+    nx, ny, dx and optional swe_params fields.  checked: the library's
+    checked variant (see Solver)."""
 
-    def __init__(self, specs, stream=None, block_cols=0, tile_rows=0):
-        L = load_library()
+    def __init__(self, specs, stream=None, block_cols=0, tile_rows=0, checked=False):
+        L = load_library(checked=checked)
         self._L = L
         n = len(specs)
         arr = (Params * n)()
@@ -384,7 +385,7 @@ class Ensemble:
         for k in range(n):
             mh = ctypes.c_void_p()
             self._check(L.swe_ensemble_member(self._h, k, ctypes.byref(mh)))
-            self.members.append(Solver._view(mh, arr[k]))
+            self.members.append(Solver._view(mh, arr[k], lib=L))
 
     def _check(self, st):
         if st != SWE_OK:

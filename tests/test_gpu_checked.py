@@ -85,3 +85,35 @@ def test_checked_build_finds_no_index_outside(swe, nx, ny, precision, bw, th, op
     assert st == 0 and st_ref == 0, (st, st_ref)
     for a, r in zip(got, ref):
         assert np.array_equal(a, r)
+
+
+def test_checked_build_ensemble(swe):
+    """The persistent ensemble kernel on the checked build: scenarios of
+    different sizes (a 1-column one among them), inflow and walls/open
+    sides, 10 steps; no index outside, members bit-identical to the
+    production build's ensemble."""
+    sizes = [(1, 40), (37, 23), (300, 140), (130, 3)]
+
+    def run(checked):
+        specs = [dict(nx=nx, ny=ny, dx=1.0, A_J=0.02, bc_e=k % 2) for k, (nx, ny) in enumerate(sizes)]
+        E = swe.Ensemble(specs, checked=checked, block_cols=128, tile_rows=16)
+        outs = []
+        for k, (m, (nx, ny)) in enumerate(zip(E.members, sizes)):
+            state, kw, rng = _case(nx, ny, seed=77 + k)
+            m.set_manning(np.array([[0.03]]), block=1 << 14)
+            src = np.zeros((ny, nx), dtype=np.uint8)
+            src[ny // 2, 0] = 1
+            m.set_sources(src, np.array([0.0, 1e6]), np.array([1.0, 1.0]))
+            m.set_state(*state)
+        E.run(10)
+        for m in E.members:
+            m.sync()
+            outs.append((m.get_state(np.float64), m.diag()["status"]))
+        E.close()
+        return outs
+
+    ref, got = run(False), run(True)
+    for (a, st_a), (r, st_r) in zip(got, ref):
+        assert st_a == 0 and st_r == 0, (st_a, st_r)
+        for x, y in zip(a, r):
+            assert np.array_equal(x, y)
