@@ -336,7 +336,8 @@ swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *tar
 swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h);
 /* Runs nwindows windows, each worth K coupled steps of bed evolution.  A
  * surrogate window saves the bed, runs one coupled step, predicts the
- * window's bed change, advances the water K/f - 1 further steps and sets the
+ * window's bed change (on the active halo tiles, as swe_surrogate_apply
+ * does), advances the water K/f - 1 further steps and sets the
  * bed to the saved bed plus the prediction (replacing what those steps did to
  * it); its bed time is f times its water time.  Every judge_every-th window instead runs K coupled
  * steps and judges the prediction against them; a judged bed-change error
