@@ -246,7 +246,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"half-wet fractal terrain {n}x{n}, dx=5 m, Manning per 64^2 block; "
-                                   f"oracle on 1024^2 windows", "grid": n},
+                                   f"oracle on its central {w}x{w} window", "grid": n},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
