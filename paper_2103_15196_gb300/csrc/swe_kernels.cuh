@@ -702,8 +702,9 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     if (c.hgs) {
         int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
         int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
-        const int nt = c.tiles_x * c.tiles_y;
-        auto cen = [&](int i) { return SWE_IN(i, nt) ? (COHERENT ? __ldcg(cen_in + i) : cen_in[i]) : 0; };
+        auto cen = [&](int i) {
+            return SWE_IN(i, c.tiles_x * c.tiles_y) ? (COHERENT ? __ldcg(cen_in + i) : cen_in[i]) : 0;
+        };
         bool active = cen(tile) > 0 || cen(by * c.tiles_x + l) > 0 || cen(by * c.tiles_x + r) > 0 ||
                       cen(d * c.tiles_x + bx) > 0 || cen(u * c.tiles_x + bx) > 0;
         if (!active) {
