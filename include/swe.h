@@ -188,6 +188,15 @@ swe_status swe_get_diag(swe_handle *h, swe_diag *out);
  * block grid size only. */
 swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, int *tiles_y);
 
+/* Block shape tuning (Sec. 3 sizes blocks for the hardware; no law): times
+ * trial_steps steps of the current state for each candidate shape (128 or
+ * 256 columns x 32..256 rows, not beyond the grid), keeps the fastest and
+ * restores the state and time exactly (results never depend on the shape;
+ * the inflow total and step counter restart as after swe_set_state).
+ * Outputs (nullable) the chosen shape.  Needs the state set (SWE_ESTATE);
+ * SWE_ENOMEM if the state copy cannot be allocated. */
+swe_status swe_autotune(swe_handle *h, int trial_steps, int *block_cols, int *tile_rows);
+
 /* One FP32 step without any device allocation.  There is no counterpart of
  * this in the paper; it is for callers that cannot allocate device memory
  * while they run: code being recorded into a CUDA graph (cudaMalloc ends the

@@ -710,3 +710,57 @@ int handle_retile(swe_handle *h, int bw, int th) {
 }
 }  // namespace swe_impl
 
+extern "C" swe_status swe_autotune(swe_handle *h, int trial_steps, int *block_cols, int *tile_rows) {
+    const SweRange range_("swe_autotune");
+    if (!h || trial_steps < 1) return fail(h, SWE_EINVAL, "swe_autotune: bad argument");
+    if (!h->state_set) return fail(h, SWE_ESTATE, "swe_autotune before swe_set_state");
+    const bool f32 = is_f32(h);
+    const size_t N = (size_t)h->c.nx * h->c.ny, es = f32 ? 4 : 8;
+    const int dt = f32 ? SWE_FP32 : SWE_FP64;
+    void *copy = nullptr;
+    if (dev_alloc(h, &copy, 4 * N * es) != cudaSuccess) return fail(h, SWE_ENOMEM, "swe_autotune: state copy");
+    char *q = (char *)copy;
+    double t0 = 0;
+    swe_status s = swe_get_state_ex(h, q, q + N * es, q + 2 * N * es, q + 3 * N * es, dt, SWE_DEVICE);
+    if (s == SWE_OK) s = swe_get_time(h, &t0);
+    auto restore = [&]() -> swe_status {
+        swe_status r = swe_set_state_ex(h, q, q + N * es, q + 2 * N * es, q + 3 * N * es, dt, SWE_DEVICE);
+        return r == SWE_OK ? swe_set_time(h, t0) : r;
+    };
+    const int bw0 = h->bw, th0 = h->c.th;
+    int best_bw = bw0, best_th = th0;
+    float best = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == SWE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) s = SWE_ECUDA;
+    const int cand_th[7] = {32, 64, 96, 128, 160, 192, 256};
+    for (int bw : {128, 256}) {
+        if (s != SWE_OK) break;
+        if (bw == 256 && h->c.nx <= 120) continue;
+        for (int th : cand_th) {
+            if (th > 32 && th >= h->c.ny + 8) break;   // one strip already covers the grid
+            if ((s = (swe_status)swe_impl::handle_retile(h, bw, th)) != SWE_OK || (s = restore()) != SWE_OK ||
+                (s = swe_run_steps(h, 1)) != SWE_OK || (s = restore()) != SWE_OK || (s = swe_run_steps(h, 1)) != SWE_OK)
+                break;   // untimed: builds the step graph and warms up
+            cudaEventRecord(e0, h->stream);
+            if ((s = swe_run_steps(h, trial_steps)) != SWE_OK) break;
+            cudaEventRecord(e1, h->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { s = SWE_ECUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if ((s = swe_sync(h)) != SWE_OK) break;
+            if (ms < best) { best = ms; best_bw = bw; best_th = th; }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // the chosen shape (the original one if a trial failed), the saved state and time
+    const swe_status rt = (swe_status)swe_impl::handle_retile(h, s == SWE_OK ? best_bw : bw0, s == SWE_OK ? best_th : th0);
+    const swe_status rs = restore();
+    dev_free(h, copy);
+    if (s == SWE_OK) s = rt != SWE_OK ? rt : rs;
+    if (s != SWE_OK) return fail(h, s, "swe_autotune failed");
+    if (block_cols) *block_cols = h->bw;
+    if (tile_rows) *tile_rows = h->c.th;
+    return SWE_OK;
+}
+

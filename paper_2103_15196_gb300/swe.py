@@ -138,6 +138,7 @@ def load_library(build_if_missing: bool = True, checked: bool = False):
         "swe_ensemble_member": [vp, ctypes.c_int, ctypes.POINTER(H)],
         "swe_ensemble_run": [vp, ctypes.c_int64],
         "swe_ensemble_autotune": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "swe_autotune": [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "swe_ensemble_set_timeout": [vp, ctypes.c_double, ctypes.c_int],
     })
     sig.update({
@@ -350,6 +351,13 @@ class Solver:
     def tile(self):
         d = self.diag()
         return d["tile_x"], d["tile_y"]
+
+    def autotune(self, trial_steps=5):
+        """Times the candidate block shapes on the current state, keeps the
+        fastest and restores the state and time; returns (block_cols, tile_rows)."""
+        bw, th = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._L.swe_autotune(self._h, int(trial_steps), ctypes.byref(bw), ctypes.byref(th)))
+        return bw.value, th.value
 
 
 class Ensemble:

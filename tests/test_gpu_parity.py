@@ -357,3 +357,37 @@ def test_error_paths(gpu):
     S.set_state(H, Z, Z, Z)   # a fresh state clears the status
     S.step()
     S.close()
+
+
+def test_autotune_restores_the_state_and_changes_no_result(gpu):
+    """swe_autotune times block shapes on the current state, keeps the
+    fastest and restores state and time exactly; the steps after it equal,
+    bit for bit, those of a solver with the default shape (results do not
+    depend on the block shape)."""
+    sc = I.half_wet(640, dx=5.0, seed=5, wet_fraction=0.5)
+    args = [np.ascontiguousarray(a, dtype=np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)]
+
+    def solver():
+        S = gpu.Solver(640, 640, 5.0, precision="fp32")
+        S.set_manning(sc.manning, block=64)
+        S.set_state(*args)
+        S.run_steps(3)
+        S.sync()
+        return S
+
+    A = solver()
+    before = A.get_state(np.float32)
+    t_before = A.diag()["t"]
+    bw, th = A.autotune(3)
+    assert bw in (128, 256) and th % 8 == 0 and 32 <= th <= 256
+    assert A.tile == (bw - 8, th)
+    for a, r in zip(A.get_state(np.float32), before):
+        assert np.array_equal(a, r)
+    assert A.diag()["t"] == t_before
+    A.run_steps(20)
+    B = solver()
+    B.run_steps(20)
+    for a, r in zip(A.get_state(np.float32), B.get_state(np.float32)):
+        assert np.array_equal(a, r)
+    A.close()
+    B.close()
