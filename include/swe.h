@@ -190,7 +190,7 @@ swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, int *tiles_
 
 /* Block shape tuning (Sec. 3 sizes blocks for the hardware; no law): times
  * trial_steps steps of the current state for each candidate shape (128 or
- * 256 columns x 32..256 rows, not beyond the grid), keeps the fastest and
+ * 256 columns x 16..256 rows, not beyond the grid), keeps the fastest and
  * restores the state and time exactly (results never depend on the shape;
  * the inflow total and step counter restart as after swe_set_state).
  * Outputs (nullable) the chosen shape.  Needs the state set (SWE_ESTATE);

@@ -732,12 +732,12 @@ extern "C" swe_status swe_autotune(swe_handle *h, int trial_steps, int *block_co
     float best = INFINITY;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s == SWE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) s = SWE_ECUDA;
-    const int cand_th[7] = {32, 64, 96, 128, 160, 192, 256};
+    const int cand_th[8] = {16, 32, 64, 96, 128, 160, 192, 256};
     for (int bw : {128, 256}) {
         if (s != SWE_OK) break;
         if (bw == 256 && h->c.nx <= 120) continue;
         for (int th : cand_th) {
-            if (th > 32 && th >= h->c.ny + 8) break;   // one strip already covers the grid
+            if (th > 16 && th >= h->c.ny + 8) break;   // one strip already covers the grid
             if ((s = (swe_status)swe_impl::handle_retile(h, bw, th)) != SWE_OK || (s = restore()) != SWE_OK ||
                 (s = swe_run_steps(h, 1)) != SWE_OK || (s = restore()) != SWE_OK || (s = swe_run_steps(h, 1)) != SWE_OK)
                 break;   // untimed: builds the step graph and warms up

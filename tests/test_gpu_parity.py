@@ -379,7 +379,7 @@ def test_autotune_restores_the_state_and_changes_no_result(gpu):
     before = A.get_state(np.float32)
     t_before = A.diag()["t"]
     bw, th = A.autotune(3)
-    assert bw in (128, 256) and th % 8 == 0 and 32 <= th <= 256
+    assert bw in (128, 256) and th % 8 == 0 and 16 <= th <= 256
     assert A.tile == (bw - 8, th)
     for a, r in zip(A.get_state(np.float32), before):
         assert np.array_equal(a, r)
