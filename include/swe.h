@@ -245,7 +245,7 @@ swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member);
  * SWE_ETIMEOUT if the launch's grid barrier gave up (see set_timeout). */
 swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
 
-/* Times each candidate block shape (128 or 256 columns x 16..128 rows) for
+/* Times each candidate block shape (128 or 256 columns x 16..192 rows) for
  * trial_steps steps on the current states, keeps the fastest, and restores
  * the states and times (step counters and inflow totals restart).  Outputs
  * (nullable) the chosen shape. */
