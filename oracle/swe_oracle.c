@@ -12,7 +12,11 @@
  * coupled Saint-Venant + Exner system of Eq. 6, with the Exner law of Eq. 1-5
  * and the stability bound of Eq. 7.  The paper does not print the discrete
  * CSPH-TVD scheme; every place where this code fixes a choice the paper leaves
- * open is marked READING and listed in the design notes.
+ * open is marked READING and listed in the design notes.  Fidelity to the
+ * authors' own discretisation is therefore parity unpinned; what pins this
+ * reading are the tests' closed forms, invariants and analytic solutions
+ * (lake at rest, conservation, Stoker/Ritter dam breaks, Manning decay, the
+ * Exner diffusion mode, HLL identities, symmetry, Eq. 7 hand cases).
  *
  * Layout: all arrays are row-major [ny][nx], x fastest, FP64.
  * Every stage is a separate full pass over an extended rectangle that carries
