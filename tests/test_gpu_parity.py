@@ -210,6 +210,56 @@ def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc):
     print("fp32 ragged per-step", bc, "worst abs err (H, Hu, Hv, b):", worst, "outflow m^3:", outflow)
 
 
+@pytest.mark.parametrize("variant", ["inflow", "rain_infiltration", "general_laws"])
+def test_fp32_kernel_variants_per_step(gpu, orc, variant):
+    """The FP32 step kernel's other compiled variants, element by element
+    against the FP64 oracle one step at a time from the same inputs on the
+    ragged 333 x 271 grid: inflow cells with a hydrograph (the source-term
+    variant), rain and infiltration fields on top, and the general transport
+    laws (A_J from Eq. 4, m = 2.5).  Same per-step FP32 bound as above."""
+    nx, ny = 333, 271
+    base = I.ensemble_scenario(max(nx, ny), seed=52, manning=0.035, peak=300.0, d50_scale=1.0)
+    H, b = base.H[:ny, :nx].astype(np.float64), base.b[:ny, :nx].astype(np.float64)
+    Hu, Hv = 0.4 * H, -0.2 * H
+    kw = dict(A_J=0.01)
+    src = rain = beta = hydro = None
+    if variant in ("inflow", "rain_infiltration"):
+        src = np.ascontiguousarray(base.src[:ny, :nx])
+        assert src.sum() > 0
+        hydro = orc.Hydrograph(base.hydro_t, base.hydro_Q)
+    if variant == "rain_infiltration":
+        rng = np.random.default_rng(52)
+        rain = rng.uniform(0.0, 2e-3, (ny, nx))
+        beta = rng.uniform(0.0, 1e-3, (ny, nx))
+    if variant == "general_laws":
+        kw.update(aj_mode=1, m_exp=2.5)
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32, **kw)
+    S.set_manning(np.full((ny, nx), 0.035), block=0)
+    if src is not None:
+        S.set_sources(src, base.hydro_t, base.hydro_Q)
+    S.set_state(H, Hu, Hv, b)
+    if rain is not None:
+        S.set_rain(rain)
+        S.set_infiltration(beta)
+    p = orc.Params(nx=nx, ny=ny, dx=base.dx, **kw)
+    ncell = np.full((ny, nx), 0.035)
+    worst = np.zeros(4)
+    for it in range(20):
+        t = S.diag()["t"]
+        st = orc.State(*(a.astype(np.float64) for a in S.get_state(np.float32)))
+        o, info = orc.step(p, st, ncell, src=src, hydro=hydro, t=t, rain=rain, beta=beta)
+        dt = S.step()
+        assert dt == pytest.approx(info.dt, rel=1e-5), it
+        got = S.get_state(np.float32)
+        for q in range(4):
+            e = np.abs(got[q].astype(np.float64) - o.arrays()[q])
+            tol = 4e-5 + (2e-5 * np.abs(o.arrays()[q]) if q in (1, 2) else 0.0)
+            worst[q] = max(worst[q], e.max())
+            assert np.all(e <= tol), (it, q, e.max())
+    S.close()
+    print("fp32 variant", variant, "worst abs err (H, Hu, Hv, b):", worst)
+
+
 @pytest.mark.parametrize("shape", [(1, 9), (9, 1), (3, 5), (130, 3)])
 @pytest.mark.parametrize("bc", [(1, 0, 0, 1), (0, 1, 1, 0), (1, 1, 1, 1)], ids=["open_wn", "open_es", "open_all"])
 def test_fp64_parity_tiny_grids_open_boundaries(gpu, orc, shape, bc):
