@@ -118,9 +118,11 @@ static double minmod(double a, double b)
 /* The limiter, exported for its unit test. */
 double orc_minmod(double a, double b) { return minmod(a, b); }
 
-/* HLL flux of a scalar advected with speed s between left and right states.
- * sL = min(uL, uR), sR = max(uL, uR) for the advective (pressure-free) flux of
- * Eq. 6; the pressure and bed-slope terms live in the source Phi. */
+/* HLL flux of one conserved quantity U with physical flux F between left and
+ * right states, for wave-speed bounds sL <= sR.  The caller passes the
+ * shallow-water bounds sL = min(uL - cL, uR - cR), sR = max(uL + cL, uR + cR)
+ * (celerity c = sqrt(g H*) on wet cells); the fluxes are the advective ones of
+ * Eq. 6, the pressure and bed-slope terms living in the source Phi. */
 double orc_hll(double UL, double UR, double FL, double FR, double sL, double sR)
 {
     if (sL >= 0.0) return FL;

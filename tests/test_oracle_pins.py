@@ -282,7 +282,7 @@ def test_manning_friction_ode(orc):
 
 # ----------------------------------------------------- Exner (Eq. 1-5)
 
-def _exner_decay_case(orc, v0, aj_mode=0, nman=0.03, H0=1.0, m_wave=3, nx=64):
+def _exner_decay_case(orc, v0, aj_mode=0, nman=0.03, H0=1.0, m_wave=3, nx=64, m_exp=2.0):
     """Frozen uniform flow along y on a 1-row grid, bed b = eps cos(k x):
     the x-direction Exner flux is pure slope diffusion C_J |J0| db/dx, so each
     Fourier mode decays by 1 - 4 (C_J |J0| dt / ((1-psi) h^2)) sin^2(k h / 2)."""
@@ -292,7 +292,7 @@ def _exner_decay_case(orc, v0, aj_mode=0, nman=0.03, H0=1.0, m_wave=3, nx=64):
     b = 0.05 * np.cos(k * x)[None, :]
     H = np.full((1, nx), H0)
     st0 = _state(orc, H, 0 * H, H * v0, b)
-    p = orc.Params(nx=nx, ny=1, dx=dx, frozen_hydro=1, aj_mode=aj_mode, A_J=0.002,
+    p = orc.Params(nx=nx, ny=1, dx=dx, frozen_hydro=1, aj_mode=aj_mode, A_J=0.002, m_exp=m_exp,
                    tile_x=nx, tile_y=1)
     st, info = orc.step(p, st0, nman)
     return p, st0, st, info, k
@@ -313,6 +313,26 @@ def test_exner_diffusion_mode_decay(orc):
         assert r < 1.0 - 1e-6
 
 
+@pytest.mark.parametrize("m", [1.5, 2.5, 3.0])
+def test_exner_diffusion_mode_decay_grass_exponent(orc, m):
+    """The Grass exponent m of Eq. 3 away from the default m = 2: a uniform
+    speed v0 carries |J0| = A_J v0^(m+1), so the cosine bed mode decays by the
+    closed-form factor with D = C_J A_J v0^(m+1) / (1 - psi).  dt itself is
+    checked against Eq. 7 written out with that D."""
+    v0, H0 = 1.7, 1.0
+    p, st0, st, info, k = _exner_decay_case(orc, v0, H0=H0, m_exp=m)
+    J0 = p.A_J * v0 ** (m + 1.0)
+    D = p.C_J * J0 / (1.0 - p.psi)
+    dt = p.cfl_K * min(p.dx / (2 * v0), p.dx / (v0 + math.sqrt(p.g * H0)), p.dx ** 2 / (2 * D), p.dt_max / p.cfl_K)
+    assert info.dt == pytest.approx(dt, rel=1e-14, abs=0), (m, info.dt, dt)
+    r = 1.0 - 4.0 * D * info.dt / p.dx ** 2 * math.sin(k * p.dx / 2) ** 2
+    assert np.allclose(st.b, r * st0.b, rtol=0, atol=1e-15), (m, r)
+    assert r < 1.0 - 1e-6
+    # a different exponent gives a measurably different decay: the pin sees m
+    r2 = 1.0 - 4.0 * (p.C_J * p.A_J * v0 ** 3 / (1.0 - p.psi)) * info.dt / p.dx ** 2 * math.sin(k * p.dx / 2) ** 2
+    assert not np.allclose(st.b, r2 * st0.b, rtol=0, atol=1e-12)
+
+
 def test_exner_shamov_gate(orc):
     """Below the Shamov critical velocity (Eq. 5) no sediment moves."""
     p = orc.Params(nx=1, ny=1)
@@ -323,11 +343,12 @@ def test_exner_shamov_gate(orc):
     assert not np.array_equal(st.b, st0.b)
 
 
+@pytest.mark.parametrize("m", [2.0, 1.5, 2.5], ids=["m2", "m1.5", "m2.5"])
 @pytest.mark.parametrize("q", [2.0, -2.0], ids=["flow_+x", "flow_-x"])
-def test_exner_advection_is_upwind(orc, q):
+def test_exner_advection_is_upwind(orc, q, m):
     """Frozen steady flow q = const over a bed hump with C_J = 0 reduces the
     Exner update (Eq. 1) to first-order upwind differencing of the Grass load
-    J0 = A_J v|v|^2 (Eq. 3) with v = q/H: backward differences for q > 0,
+    J0 = A_J v|v|^m (Eq. 3) with v = q/H: backward differences for q > 0,
     forward ones for q < 0.  The hump's centroid moves downstream and the
     bed volume is conserved."""
     nx, dx = 200, 1.0
@@ -336,10 +357,10 @@ def test_exner_advection_is_upwind(orc, q):
     eta0 = 2.0
     H = eta0 - b
     st0 = _state(orc, H, q + 0 * H, 0 * H, b)
-    p = orc.Params(nx=nx, ny=1, dx=dx, frozen_hydro=1, C_J=0.0, A_J=0.01, tile_x=nx, tile_y=1)
+    p = orc.Params(nx=nx, ny=1, dx=dx, frozen_hydro=1, C_J=0.0, A_J=0.01, m_exp=m, tile_x=nx, tile_y=1)
     st, info = orc.step(p, st0, 0.03)
     v = q / H[0]
-    J = p.A_J * v * v * v
+    J = p.A_J * v * np.abs(v) ** m
     db = st.b[0] - b[0]
     c = info.dt / (dx * (1.0 - p.psi))
     inner = slice(5, nx - 5)
