@@ -105,21 +105,82 @@ def _profile_traffic(n):
 ISSUE_LANES_PER_CLOCK = 152 * 4 * 32
 
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes): SM
+    clock, its maximum, power draw and the active clock-event reasons."""
+    SM = 1                                   # NVML_CLOCK_SM
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, pci_bus_id):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle for " + pci_bus_id)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        ct = self.ct
+        sm, mx, mw, r = ct.c_uint(0), ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, ct.byref(sm))
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ct.byref(mx))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+        self.reasons_fn(self.h, ct.byref(r))
+        names = [v for k, v in self.BITS.items() if r.value & k]
+        return float(sm.value), float(mx.value), mw.value / 1000.0, names
+
+
 class Clocks:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples the SM clock, power and clock-event reasons every 100 ms on a
+    host thread (NVML, read only; nvidia-smi as a fallback), started before
+    the warm-up.  summary() keeps the samples taken between start() and
+    stop(), i.e. during the timed region."""
 
     def __init__(self, index):
         self.index = str(index)
+        self.pci = None
         try:
             import torch
             pr = torch.cuda.get_device_properties(index)
-            self.index = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            self.pci = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            self.index = self.pci
         except Exception:
             pass
-        self.samples = []
+        self.samples = []           # (host time, sm_mhz, max_mhz, watts, [reasons])
         self.proc = None
+        self.nvml = None
+        self.source = None
+        self.t0 = None
+        self.t1 = None
+        self._halt = threading.Event()
+
+    def wait_first(self, timeout=20.0):
+        """Blocks until the sampler has delivered a sample (or timeout s)."""
+        t = time.time()
+        while (self.proc or self.nvml) and not self.samples and time.time() - t < timeout:
+            time.sleep(0.05)
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
 
     def __enter__(self):
+        try:
+            self.nvml = _Nvml(self.pci) if self.pci else None
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.source = "nvml"
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
@@ -127,19 +188,34 @@ class Clocks:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
         return self
 
+    def _poll(self):
+        while not self._halt.is_set():
+            try:
+                self.samples.append((time.time(),) + self.nvml.sample())
+            except Exception:
+                return
+            self._halt.wait(0.1)
+
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 7:
-                self.samples.append(parts)
+            s = [p.strip() for p in line.split(",")]
+            if len(s) >= 7 and s[0].replace(".", "").isdigit():
+                try:
+                    self.samples.append((time.time(), float(s[0]), float(s[1]), float(s[2]),
+                                         [names[i] for i in range(4) if s[3 + i].lower() == "active"]))
+                except ValueError:
+                    pass
 
     def __exit__(self, *a):
+        self._halt.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -148,14 +224,17 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+        t0 = self.t0 if self.t0 is not None else -float("inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        samples = [x for x in self.samples if t0 <= x[0] <= t1]
+        if not samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
+        sm = [x[1] for x in samples]
+        reasons = sorted({r for x in samples for r in x[4]})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(x[2] for x in samples),
+                "power_w_max": max(x[3] for x in samples), "reasons": reasons, "samples": len(samples),
+                "source": self.source}
 
 
 def _issue_object(gcell_s, clocks):
@@ -567,17 +646,21 @@ def run_ours(args):
             dist.barrier()
 
     # --- device-timed region, inputs resident
+    clk = Clocks(local).__enter__()
+    clk.wait_first()
     S.run_steps(W)
     S.sync()
     d0 = S.diag()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        S.run_steps(K)
-        ev1.record(stream)
-        ev1.synchronize()
+    clk.start()
+    ev0.record(stream)
+    S.run_steps(K)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk.stop()
+    clk.__exit__(None, None, None)
     torch.cuda.synchronize()
     barrier()
     ms = _max_over_ranks(ev0.elapsed_time(ev1), world)

@@ -198,26 +198,27 @@ swe_status swe_get_census(swe_handle *h, int32_t *out, int *tiles_x, int *tiles_
 swe_status swe_autotune(swe_handle *h, int trial_steps, int *block_cols, int *tile_rows);
 
 /* One FP32 step without any device allocation.  There is no counterpart of
- * this in the paper; it is for callers that cannot allocate device memory
- * while they run: code being recorded into a CUDA graph (cudaMalloc ends the
- * capture), real-time loops that cannot afford cudaMalloc's implicit device
- * synchronisation, and applications whose own allocator owns all device
- * memory.  The caller owns both state buffers: state_in and state_out are
+ * this in the paper.  It is for callers that cannot allocate device memory
+ * while they run: real-time loops that cannot afford cudaMalloc's implicit
+ * device synchronisation, and applications whose own allocator owns all
+ * device memory (a pool reserved at start-up leaves nothing for a library to
+ * take).  The caller owns both state buffers: state_in and state_out are
  * distinct, 16-byte aligned device arrays of nx*ny cells, each cell four
- * floats {H, Hu, Hv, b} (row-major [ny][nx]).  state_in is read (and the
- * momentum of its dry cells set to zero, as swe_set_state does); state_out
- * receives the state one Eq. 7 time step later (t = 0 for the hydrograph; no
- * sources; uniform Manning n = manning_n).  *dt_taken (host, nullable) gets
- * the step.  p->precision must be SWE_FP32.
- * Working memory (HGS census, skip flags, step bookkeeping) comes from a
- * fixed 1 MiB array inside the library, one copy per GPU, kept until the
- * process exits; grids whose working set does not fit (e.g. beyond about
- * 32768 x 32768 with the default blocks) return SWE_EINVAL.  All calls on a
- * GPU share that array: calls whose work overlaps on one GPU (say, on two
- * streams) race and must be serialised by the caller.  The first call on a
- * device looks the array up (cudaGetSymbolAddress) with that device current;
- * make it before any stream capture.  Synchronises cuda_stream. */
-swe_status swe_step_noalloc(const swe_params *p, double manning_n, const void *state_in,
+ * floats {H, Hu, Hv, b} (row-major [ny][nx]).  state_in is read, and the
+ * momentum of its dry cells is set to zero in place (as swe_set_state does);
+ * state_out receives the state one Eq. 7 time step later (t = 0 for the
+ * hydrograph; no sources; uniform Manning n = manning_n).  *dt_taken (host,
+ * nullable) gets the step.  p->precision must be SWE_FP32.
+ * Working memory (HGS census, skip flags, block list, step bookkeeping) comes
+ * from a fixed 1 MiB array inside the library, one copy per GPU, kept until
+ * the process exits.  A grid fits while 13 bytes per HGS block plus 4 bytes
+ * per row stay below about 1 MiB (32768 x 32768 with the default blocks needs
+ * 0.55 MiB); larger grids return SWE_EINVAL.  All calls on a GPU share that
+ * array: calls whose work overlaps on one GPU (say, on two streams) race and
+ * must be serialised by the caller.  The first call on a device looks the
+ * array up (cudaGetSymbolAddress) with that device current; make it before
+ * any stream capture.  Synchronises cuda_stream. */
+swe_status swe_step_noalloc(const swe_params *p, double manning_n, void *state_in,
                             void *state_out, void *cuda_stream, double *dt_taken);
 
 /* ---------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Generic launchers; each precision's translation unit includes this file and
 // instantiates the templates for its own state type.
 #pragma once
+#include <atomic>
+
 #include "swe_kernels.cuh"
 
 namespace swe_impl {
@@ -15,13 +17,19 @@ template <typename T> size_t step_smem_bytes(int bw) {
 // (SRC), the general transport laws (GEN).
 template <typename T, int BW, bool SRC, bool GEN>
 static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
-    static bool configured = false;
+    // the shared-memory opt-in is a per-device function attribute: one bit
+    // per device (devices beyond 64 set it on every launch)
+    static std::atomic<unsigned long long> configured{0};
     const size_t smem = sizeof(StepSmem<T, BW>);
     auto kern = step_kernel<T, BW, SRC, GEN>;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (!bit || !(configured.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.fetch_or(bit, std::memory_order_release);
     }
     compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
     kern<<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);

@@ -3,19 +3,23 @@
 // this library instead of from cudaMalloc.
 //
 // Who needs this: callers that must not allocate device memory once they are
-// running.  Examples are code that records its work into a CUDA graph (an
-// allocation would end the capture), real-time loops where cudaMalloc's
-// implicit device synchronisation would stall other streams, and host
-// applications whose own memory manager owns all device memory.  Such a
-// caller passes the input and output state; everything else lives in
-// `g_scratch` below.
+// running.  Examples are real-time loops where cudaMalloc's implicit device
+// synchronisation would stall the other streams of the application, and host
+// applications whose own memory manager owns all device memory (a pool sized
+// at start-up, with nothing left for a library to take).  Such a caller
+// passes the input and output state; everything else lives in `g_scratch`
+// below.
 //
 // Limits and sharing rules:
-//   * The array holds SWE_NOALLOC_SCRATCH_BYTES (1 MiB).  A grid fits when
-//     its HGS census (two int per block), skip flags (one byte per block) and
-//     per-row source table (one int per row) fit besides ~1 KB of
-//     bookkeeping: 32768 x 32768 cells with the default blocks needs 0.44 MiB.
-//     Larger grids are rejected with SWE_EINVAL.
+//   * The array holds SWE_NOALLOC_SCRATCH_BYTES (1 MiB), carved into the step
+//     bookkeeping (~0.2 KB), two censuses (one int per HGS block each), the
+//     skip flags (one byte per block), the block work list (one int per block
+//     plus two), the per-row source table (one int per row plus one) and the
+//     Manning constants, each region rounded up to 256 bytes.  With the
+//     default blocks (248 x 32 cells below 2^22 cells, 248 x 64 below 2^26,
+//     248 x 128 above) a 32768 x 32768 grid has 34,048 blocks and needs about
+//     0.55 MiB; a grid fits while 13 bytes per block + 4 bytes per row stay
+//     below ~1 MiB.  Larger grids are rejected with SWE_EINVAL.
 //   * Every GPU that loads the library holds its own copy of the array until
 //     the process exits.  All calls on one GPU share it and it keeps the last
 //     call's contents; each call first resets the parts that must start from
@@ -24,9 +28,12 @@
 //   * The first call on a device looks the array's address up with
 //     cudaGetSymbolAddress while that device is current; make that first
 //     call before any stream capture begins.
+//   * state_in is modified: the momentum of its dry cells is set to zero in
+//     place, as swe_set_state does for the library's own buffers.
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
 
 #include "../../include/swe.h"
 #include "swe_internal.h"
@@ -42,6 +49,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;   // guards the lookups from several host threads
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -58,6 +66,7 @@ swe_status scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return err(SWE_ECUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return err(SWE_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
@@ -70,7 +79,7 @@ swe_status scratch_address(void **out) {
 
 }  // namespace
 
-extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, const void *state_in,
+extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, void *state_in,
                                        void *state_out, void *cuda_stream, double *dt_taken) {
     const SweRange range_("swe_step_noalloc");
     if (!pp || !state_in || !state_out || state_in == state_out) return err(SWE_EINVAL, "bad pointer argument");
@@ -113,7 +122,7 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     c.eps_f = float_floor(p.eps_wet);
     swe_fill_f32(c);
 
-    // carve the scratch: bookkeeping | census x2 | skip flags | source rows | Manning tables
+    // carve the scratch: bookkeeping | census x2 | skip flags | work list | source rows | Manning tables
     const size_t ntiles = (size_t)c.tiles_x * c.tiles_y;
     const size_t off_dev = 0;
     const size_t off_cen0 = align256(off_dev + sizeof(SweDev));
@@ -131,7 +140,7 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, c
     if (s != SWE_OK) return s;
 
     SweBufs b{};
-    b.buf[0] = const_cast<void *>(state_in);
+    b.buf[0] = state_in;
     b.buf[1] = state_out;
     b.census[0] = (int *)(base + off_cen0);
     b.census[1] = (int *)(base + off_cen1);

@@ -131,6 +131,7 @@ def load_library(build_if_missing: bool = True, checked: bool = False):
         "swe_get_diag": [H, ctypes.POINTER(Diag)],
         "swe_get_census": [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
+        "swe_step_noalloc": [ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, dp],
     }
     sig.update({
         "swe_ensemble_create": [ctypes.c_int, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
@@ -146,6 +147,7 @@ def load_library(build_if_missing: bool = True, checked: bool = False):
         "swe_surrogate_create": [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(vp)],
         "swe_surrogate_destroy": [vp],
         "swe_surrogate_set_norm": [vp, ctypes.POINTER(ctypes.c_float)],
+        "swe_surrogate_set_loss": [vp, ctypes.c_int],
         "swe_surrogate_forward": [vp, vp, vp, ctypes.c_int],
         "swe_surrogate_train_step": [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)],
         "swe_surrogate_params": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int],
@@ -165,6 +167,7 @@ def load_library(build_if_missing: bool = True, checked: bool = False):
         f.restype = ctypes.c_int
     L.swe_last_error.argtypes = [H]
     L.swe_last_error.restype = ctypes.c_char_p
+    L.swe_signatures = dict(sig, swe_last_error=[H])
     _libs[checked] = L
     return L
 

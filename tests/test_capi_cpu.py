@@ -16,6 +16,14 @@ def test_library_builds_and_exports_header_symbols():
     assert not missing, missing
 
 
+def test_binding_declares_every_header_function():
+    """The ctypes binding gives every function of include/swe.h its argument
+    and return types (none is left to ctypes' default int conversion)."""
+    L = swe.load_library()
+    missing = [n for n in swe.header_functions() if n not in L.swe_signatures]
+    assert not missing, missing
+
+
 def test_params_default_host_only():
     L = swe.load_library()
     p = swe.Params()

@@ -109,3 +109,56 @@ def test_ensemble_barrier_gives_up_with_a_status(swe):
         for a, b in zip(m.get_state(np.float32), ref):
             assert np.array_equal(a, b), k
     E.close()
+
+
+def test_ensemble_members_match_the_oracle_per_step(swe, orc):
+    """Each member of one persistent ensemble launch against the FP64 oracle,
+    one step at a time from the member's own FP32 state, element by element,
+    within the per-step FP32 bound of the single-grid parity tests (4e-5 m on
+    H and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta); dt (Eq. 7) per member.
+    Members of uneven size: a ragged 333 x 271 grid with inflow (2 x 9 blocks
+    of 248 x 32, ragged right and bottom), a 200 x 200 grid without sources,
+    a tall 96 x 312 grid with inflow, a 64 x 64 grid; every one drifts so the
+    Grass load (Eq. 3) and the Exner update run."""
+    shapes = [(333, 271, True, (0.8, -0.3)), (200, 200, False, (-0.6, 0.7)), (96, 312, True, (0.3, 0.9)),
+              (64, 64, False, (0.9, 0.2))]
+    members = []
+    for k, (nx, ny, inflow, (ux, uy)) in enumerate(shapes):
+        base = I.ensemble_scenario(max(nx, ny), seed=610 + k, manning=0.03 + 0.005 * k, peak=400.0,
+                                   d50_scale=0.7 + 0.2 * k)
+        H = np.ascontiguousarray(base.H[:ny, :nx], dtype=np.float64)
+        b = np.ascontiguousarray(base.b[:ny, :nx], dtype=np.float64)
+        src = None
+        if inflow:
+            src = np.ascontiguousarray(base.src[:ny, :nx])
+            assert src.sum() > 0
+        members.append(dict(nx=nx, ny=ny, dx=base.dx, d50=base.d50, n=0.03 + 0.005 * k, H=H, Hu=ux * H,
+                            Hv=uy * H, b=b, src=src, ht=base.hydro_t, hq=base.hydro_Q))
+    E = swe.Ensemble([dict(nx=m["nx"], ny=m["ny"], dx=m["dx"], d50=m["d50"], A_J=0.01) for m in members],
+                     block_cols=256, tile_rows=32)
+    for h, m in zip(E.members, members):
+        h.set_manning(np.full((m["ny"], m["nx"]), m["n"]), block=0)
+        if m["src"] is not None:
+            h.set_sources(m["src"], m["ht"], m["hq"])
+        h.set_state(m["H"], m["Hu"], m["Hv"], m["b"])
+    worst = np.zeros((len(members), 4))
+    moved = np.zeros(len(members))
+    for it in range(12):
+        before = [(orc.State(*(a.astype(np.float64) for a in h.get_state(np.float32))), h.t) for h in E.members]
+        E.run(1)
+        for k, (h, m) in enumerate(zip(E.members, members)):
+            st, t = before[k]
+            p = orc.Params(nx=m["nx"], ny=m["ny"], dx=m["dx"], d50=m["d50"], A_J=0.01)
+            hydro = orc.Hydrograph(m["ht"], m["hq"]) if m["src"] is not None else None
+            o, info = orc.step(p, st, np.full((m["ny"], m["nx"]), m["n"]), src=m["src"], hydro=hydro, t=t)
+            assert h.t - t == pytest.approx(info.dt, rel=1e-5), (it, k)
+            got = h.get_state(np.float32)
+            moved[k] = max(moved[k], np.abs(o.b - st.b).max())
+            for q in range(4):
+                e = np.abs(got[q].astype(np.float64) - o.arrays()[q])
+                tol = 4e-5 + (2e-5 * np.abs(o.arrays()[q]) if q in (1, 2) else 0.0)
+                worst[k, q] = max(worst[k, q], e.max())
+                assert np.all(e <= tol), (it, k, q, e.max())
+    E.close()
+    assert np.all(moved > 1e-7), moved   # the bed moves in every member
+    print("ensemble vs oracle, worst abs err per member (H, Hu, Hv, b):", worst.tolist())

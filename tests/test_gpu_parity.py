@@ -4,7 +4,9 @@ Tolerances:
   * FP64 build, per step from identical inputs: relative L-infinity <= 1e-11
     (H against max|H|, momenta against max|H| sqrt(g max|H|), b against
     max(max|b|, 1e-3)); dt to 1e-13; census bit-exact.
-  * FP32 build after a config's full run: relative L1 <= 1e-4 on H and b.
+  * FP32 build after a config's full run: relative L1 <= 1e-4 on H and b,
+    and <= 5e-4 on the bed change b - b0 (the Grass load is cubic in the
+    velocity: ~3x the water state's relative error).
   * FP32 single step at full size, sampled windows: the per-step bound derived
     from FP32 rounding of the largest intermediate (the free surface
     eta <= ~25 m: ulp 2e-6) times the ~10 roundings on its path: 4e-5 m on H
@@ -341,6 +343,12 @@ def test_fp32_flood_channel_2048_full_run(gpu):
           f"oracle {float(ref['inflow']):.6e}")
     assert abs(n_gpu - int(ref["steps"])) <= 2
     assert relH <= 1e-4 and relb <= 1e-4
+    # The bed change carries the Exner physics (relative L1 of b is dominated
+    # by the 0-20 m terrain and cannot see it).  Its bound: the Grass load is
+    # cubic in the velocity, so its relative error is ~3x that of the water
+    # state (bounded by 1e-4 above); 5e-4 also covers the few cells whose
+    # Shamov gate switches one step apart.  A wrong Exner term gives O(1).
+    assert rel_db <= 5e-4, rel_db
     S.close()
 
 
