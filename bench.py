@@ -765,7 +765,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-hgs-flood", action="store_true")
     ap.add_argument("--hgs-steps", type=int, default=200)
-    ap.add_argument("--hgs-tile-rows", type=int, default=64, help="block strip height of the dry-start flood leg")
+    ap.add_argument("--hgs-tile-rows", type=int, default=32, help="block strip height of the dry-start flood leg")
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-surrogate", action="store_true")

@@ -242,8 +242,11 @@ swe_status swe_ensemble_destroy(swe_ensemble *e);
 swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member);
 
 /* Advances every scenario by nsteps steps of its own Eq. 7 dt (no t_end clip)
- * in one persistent cooperative launch.  Every scenario's state must be set.
- * SWE_ETIMEOUT if the launch's grid barrier gave up (see set_timeout). */
+ * in one persistent launch.  Work items (scenario, block) are scheduled by
+ * dataflow: a scenario's next step starts as soon as its own previous step
+ * is complete, with no barrier across scenarios.  Every scenario's state must
+ * be set.  SWE_ETIMEOUT if a block's wait for a scenario's step gave up (see
+ * set_timeout). */
 swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
 
 /* Times each candidate block shape (128 or 256 columns x 16..192 rows) for
@@ -252,11 +255,12 @@ swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
  * (nullable) the chosen shape. */
 swe_status swe_ensemble_autotune(swe_ensemble *e, int trial_steps, int *block_cols, int *tile_rows);
 
-/* Time limit of the persistent launch's grid barrier (default 2 s), after
- * which every block stops and swe_ensemble_run returns SWE_ETIMEOUT with the
- * context still usable.  extra_arrivals > 0 makes the barrier wait for that
- * many blocks that do not exist: a test hook that exercises the time limit
- * (the scenarios' states are then undefined).  Use 0 otherwise. */
+/* Time limit of each wait of the persistent launch for a scenario's step
+ * (default 2 s), after which every block stops and swe_ensemble_run returns
+ * SWE_ETIMEOUT with the context still usable.  extra_arrivals > 0 makes every
+ * scenario step wait for that many work items that do not exist: a test hook
+ * that exercises the time limit (the scenarios' states are then undefined).
+ * Use 0 otherwise. */
 swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, int extra_arrivals);
 
 /* ---------------------------------------------------------------------

@@ -608,14 +608,39 @@ __global__ void loss_grad(const float *__restrict__ out, const float *__restrict
 
 // Solver state (AoS float4 {H, Hu, Hv, b}, nx x ny) -> NHWC8 BF16 tiles of
 // T x T (tile (tx, ty) of the domain -> batch index ty * ntx + tx), zeros
-// beyond the domain.  Channels: (H, Hu, Hv, b) normalised as
-// (x - norm[j]) / norm[4 + j]; the cell velocity (u, v) / norm[10]; and the
-// Grass load direction of Eq. 3 with m = 2, v |v|^2, where the Shamov gate of
-// Eq. 5 is open (|v|^6 > ksh H), over norm[11].  Dry cells: zero velocity.
+// beyond the domain.  The channels (see cell_features): (H, b) normalised as
+// (x - norm[j]) / norm[j + 1], the cell velocity (u, v) / norm[4], the
+// Shamov ratio |v| / v_k of Eq. 5, the second difference of the bed over the
+// window's two coupled steps, their linear extrapolation p, and the activity
+// mask.  Dry cells: zero velocity and ratio.
 constexpr int kActR = 4;   // Chebyshev radius of the activity mask
 
 __device__ __forceinline__ size_t tile_index(int x, int y, int T, int ntx) {
     return ((size_t)(y / T) * ntx + x / T) * T * T + (size_t)(y % T) * T + x % T;
+}
+
+// Channels 0-6 of the network input for one cell with state c, the bed b0 at
+// the window's start and b1 after its first coupled step (c.w is the bed
+// after the second): 0, 1 (H, b) normalised; 2, 3 the velocity (u, v) /
+// norm[4]; 4 the Shamov ratio |v| / v_k = (|v|^6 / (C_Sh^6 d50^2 H))^(1/6)
+// (Eq. 5), at most 4; 5 the second difference (b2 - b1) - (b1 - b0) and 6 the
+// two-step change b2 - b0, both over 2 norm[7]: in output units, channel 6
+// is the linear extrapolation of the two steps to the window, and channel
+// 6 - channel 5 that of the first step alone.
+__device__ __forceinline__ void cell_features(const float4 c, float b0, float b1, const float *__restrict__ norm,
+                                              float eps, float ksh, float f[8]) {
+    f[0] = (c.x - norm[0]) / norm[1];
+    f[1] = (c.w - norm[2]) / norm[3];
+    if (c.x > eps) {
+        const float u = c.y / c.x, v = c.z / c.x, s2 = u * u + v * v;
+        f[2] = u / norm[4];
+        f[3] = v / norm[4];
+        const float r6 = (s2 * s2 * s2) / (ksh * c.x);
+        f[4] = fminf(exp2f(log2f(r6) * (1.0f / 6.0f)), 4.f);
+    }
+    const float h7 = 2.f * norm[7];
+    f[5] = ((c.w - b1) - (b1 - b0)) / h7;
+    f[6] = (c.w - b0) / h7;
 }
 
 // Row pass of the activity mask: act[y][x] = 1 if a cell of row y within
@@ -635,8 +660,8 @@ __global__ void activity_rows(const float4 *__restrict__ state, int nx, int ny, 
 // Network input tiles (channels: see the surrogate's header comment); the
 // column pass of the activity mask is done here.
 __global__ void pack_state(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ norm,
-                           float eps, float ksh, const float *__restrict__ bsave, const uint8_t *__restrict__ act,
-                           __nv_bfloat16 *__restrict__ X, size_t total) {
+                           float eps, float ksh, const float *__restrict__ bsave, const float *__restrict__ bsave1,
+                           const uint8_t *__restrict__ act, __nv_bfloat16 *__restrict__ X, size_t total) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t plane = (size_t)T * T;
         const int bt = (int)(i / plane);
@@ -645,16 +670,7 @@ __global__ void pack_state(const float4 *__restrict__ state, int nx, int ny, int
         __align__(16) __nv_bfloat16 o[8];
         float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (x < nx && y < ny) {
-            const float4 c = state[(size_t)y * nx + x];
-            f[0] = (c.x - norm[0]) / norm[1];
-            f[1] = (c.w - norm[2]) / norm[3];
-            if (c.x > eps) {
-                const float u = c.y / c.x, v = c.z / c.x, s2 = u * u + v * v;
-                f[2] = u / norm[4];
-                f[3] = v / norm[4];
-                if (s2 * s2 * s2 > ksh * c.x) { f[4] = u * s2 / norm[5]; f[5] = v * s2 / norm[5]; }
-            }
-            f[6] = (c.w - bsave[i]) / norm[7];
+            cell_features(state[(size_t)y * nx + x], bsave[i], bsave1[i], norm, eps, ksh, f);
             uint8_t a = 0;
             for (int yy = max(0, y - kActR); yy <= min(ny - 1, y + kActR); ++yy) a |= act[(size_t)yy * nx + x];
             f[7] = a ? 1.f : 0.f;
@@ -696,8 +712,8 @@ constexpr int kTC = kTI - 2 * kHalo;
 __device__ __forceinline__ int halo_origin(int t, int n) { return min(max(t * kTC - kHalo, 0), n - kTI); }
 
 // chg: 1 where the bed differs from the saved bed (row-major); pcell: the
-// linear extrapolation (b - b_saved) / norm[7] rounded to BF16 as the network
-// reads it (tile layout of the saved bed).
+// linear extrapolation (b - b_saved) / (2 norm[7]) of the two coupled steps,
+// rounded to BF16 as the network reads it (tile layout of the saved bed).
 __global__ void bed_change(const float4 *__restrict__ state, int nx, int ny, int T, int ntx,
                            const float *__restrict__ bsave, const float *__restrict__ norm, uint8_t *__restrict__ chg,
                            float *__restrict__ pcell) {
@@ -707,7 +723,7 @@ __global__ void bed_change(const float4 *__restrict__ state, int nx, int ny, int
         const size_t j = tile_index(x, y, T, ntx);
         const float b = state[i].w, b0 = bsave[j];
         chg[i] = b != b0;
-        pcell[j] = __bfloat162float(__float2bfloat16((b - b0) / norm[7]));
+        pcell[j] = __bfloat162float(__float2bfloat16((b - b0) / (2.f * norm[7])));
     }
 }
 
@@ -772,8 +788,9 @@ __global__ void __launch_bounds__(1024) compact_tiles(int *__restrict__ flag, in
 // Network input (NHWC8 BF16, the channels of pack_state) of the active tiles
 // list[first .. first + nimg): kTI x kTI pixels each.
 __global__ void gather_tiles(const float4 *__restrict__ state, int nx, int ny, int T, int ntx, const float *__restrict__ norm,
-                             float eps, float ksh, const float *__restrict__ pcell, const uint8_t *__restrict__ actr,
-                             const int *__restrict__ list, int first, int nimg, int ntcx, __nv_bfloat16 *__restrict__ X) {
+                             float eps, float ksh, const float *__restrict__ bsave, const float *__restrict__ bsave1,
+                             const uint8_t *__restrict__ actr, const int *__restrict__ list, int first, int nimg,
+                             int ntcx, __nv_bfloat16 *__restrict__ X) {
     const size_t total = (size_t)nimg * kTI * kTI;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / (kTI * kTI)), r = (int)(i % (kTI * kTI));
@@ -782,16 +799,8 @@ __global__ void gather_tiles(const float4 *__restrict__ state, int nx, int ny, i
         __align__(16) __nv_bfloat16 o[8];
         float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         {
-            const float4 c = state[(size_t)y * nx + x];
-            f[0] = (c.x - norm[0]) / norm[1];
-            f[1] = (c.w - norm[2]) / norm[3];
-            if (c.x > eps) {
-                const float u = c.y / c.x, v = c.z / c.x, s2 = u * u + v * v;
-                f[2] = u / norm[4];
-                f[3] = v / norm[4];
-                if (s2 * s2 * s2 > ksh * c.x) { f[4] = u * s2 / norm[5]; f[5] = v * s2 / norm[5]; }
-            }
-            f[6] = pcell[tile_index(x, y, T, ntx)];
+            const size_t j = tile_index(x, y, T, ntx);
+            cell_features(state[(size_t)y * nx + x], bsave[j], bsave1[j], norm, eps, ksh, f);
             uint8_t a = 0;
             for (int yy = max(0, y - kActR); yy <= min(ny - 1, y + kActR); ++yy) a |= actr[(size_t)yy * nx + x];
             f[7] = a ? 1.f : 0.f;
@@ -864,6 +873,7 @@ struct swe_surrogate {
     NnLayer L[6];
     __nv_bfloat16 *X0 = nullptr, *A[5] = {}, *dA[5] = {}, *dOut = nullptr;
     float *out = nullptr, *partial = nullptr, *loss = nullptr, *norm = nullptr, *tgt = nullptr, *bsave = nullptr;
+    float *bsave1 = nullptr;   // the bed after the window's first coupled step
     int *err = nullptr;
     size_t partial_floats = 0;
     long adam_t = 0;
@@ -1029,6 +1039,7 @@ extern "C" swe_status swe_surrogate_create(int tile, int max_batch, uint64_t see
     if (e == cudaSuccess) e = salloc(s, (void **)&s->out, pix * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->tgt, pix * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->bsave, pix * 4);
+    if (e == cudaSuccess) e = salloc(s, (void **)&s->bsave1, pix * 4);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->act, pix);
     s->partial_floats = maxpart * (size_t)max_batch * ((tile + kWgradRows - 1) / kWgradRows);
     if (e == cudaSuccess) e = salloc(s, (void **)&s->partial, s->partial_floats * 4);
@@ -1247,7 +1258,7 @@ void launch_pack(swe_surrogate *s, const Coupling &k, __nv_bfloat16 *X) {
     const size_t n = (size_t)k.c->nx * k.c->ny;
     activity_rows<<<grid_n(n), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->bsave, s->act);
     pack_state<<<grid_n(k.total), 256, 0, s->stream>>>((const float4 *)k.cur, k.c->nx, k.c->ny, s->T, k.ntx, s->norm,
-                                                       k.c->eps_f, k.c->f.ksh, s->bsave, s->act, X, k.total);
+                                                       k.c->eps_f, k.c->f.ksh, s->bsave, s->bsave1, s->act, X, k.total);
 }
 
 // The network's prediction for every cell of the coupled domain into
@@ -1293,7 +1304,8 @@ swe_status predict_tiles(swe_surrogate *s, const Coupling &k) {
         const int nimg = std::min(cap, count - first);
         if (nimg > 0) {
             gather_tiles<<<grid_n((size_t)nimg * kTI * kTI), 256, 0, s->stream>>>(
-                st, nx, ny, s->T, k.ntx, s->norm, k.c->eps_f, k.c->f.ksh, s->pcell, s->act, s->tlist, first, nimg, ntcx, s->X0);
+                st, nx, ny, s->T, k.ntx, s->norm, k.c->eps_f, k.c->f.ksh, s->bsave, s->bsave1, s->act, s->tlist, first,
+                nimg, ntcx, s->X0);
             if (forward_all(s, s->X0, s->out, nimg, kTI) != cudaSuccess) return SWE_ECUDA;
         }
         scatter_pred<<<grid_n(n), 256, 0, s->stream>>>(nx, ny, s->T, k.ntx, s->out, s->tslot, ntcx, first, nimg, s->predc);
@@ -1331,6 +1343,15 @@ extern "C" swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h) {
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
+extern "C" swe_status swe_surrogate_save_mid(swe_surrogate *s, swe_handle *h) {
+    Coupling k;
+    if (!couple(s, h, k)) return SWE_EINVAL;
+    swe_status st = after_solver(s, k);
+    if (st != SWE_OK) return st;
+    launch_save(s, k, s->bsave1);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}
+
 extern "C" swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target) {
     Coupling k;
     if (!target || !couple(s, h, k)) return SWE_EINVAL;
@@ -1355,7 +1376,8 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
                                        double bound, swe_surrogate_stats *st) {
     const SweRange range_("swe_surrogate_run");
     Coupling k;
-    if (!st || nwindows < 0 || K < 2 || f < 1 || (K % f) || judge_every < 1 || !(bound > 0) || !couple(s, h, k))
+    if (!st || nwindows < 0 || K < 2 || f < 1 || (K % f) || K / f < 2 || judge_every < 1 || !(bound > 0) ||
+        !couple(s, h, k))
         return SWE_EINVAL;
     double *dsum = nullptr;
     float *last = nullptr;
@@ -1364,11 +1386,15 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
     cudaMemsetAsync(last, 0, k.total * 4, s->stream);
     double err_sum = 0, zero_sum = 0, pers_sum = 0, lin_sum = 0;
     swe_status rc = SWE_OK;
-    // the network's prediction from the state one coupled step into the window
-    auto first_step_and_predict = [&]() -> swe_status {
+    // the network's prediction from the state two coupled steps into the
+    // window (the beds at its start and after its first step saved)
+    auto first_steps_and_predict = [&]() -> swe_status {
         swe_status r;
         if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
         launch_save(s, k, s->bsave);
+        if ((r = before_solver(s, k)) != SWE_OK || (r = swe_run_steps(h, 1)) != SWE_OK) return r;
+        if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
+        launch_save(s, k, s->bsave1);
         if ((r = before_solver(s, k)) != SWE_OK || (r = swe_run_steps(h, 1)) != SWE_OK) return r;
         if (!couple(s, h, k) || (r = after_solver(s, k)) != SWE_OK) return r == SWE_OK ? SWE_EINVAL : r;
         if ((r = predict_tiles(s, k)) != SWE_OK) return r;
@@ -1386,8 +1412,8 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             st->water_time += t1 - t0;
             ++st->plain_windows;
         } else if (w % judge_every == 0) {                       // judged window: K coupled steps
-            if ((rc = first_step_and_predict()) != SWE_OK) break;
-            if ((rc = swe_run_steps(h, K - 1)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
+            if ((rc = first_steps_and_predict()) != SWE_OK) break;
+            if ((rc = swe_run_steps(h, K - 2)) != SWE_OK || (rc = swe_get_time(h, &t1)) != SWE_OK) break;
             if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
             if ((rc = check_err(s)) != SWE_OK) break;
             launch_save(s, k, s->tgt);
@@ -1416,10 +1442,10 @@ extern "C" swe_status swe_surrogate_run(swe_surrogate *s, swe_handle *h, int nwi
             st->water_time += t1 - t0;
             if (err > bound) { st->mode = 1; st->takeover_window = w; }
         } else {                                                 // surrogate window
-            if ((rc = first_step_and_predict()) != SWE_OK) break;
+            if ((rc = first_steps_and_predict()) != SWE_OK) break;
             // the remaining water steps run the coupled step as it is: the bed
             // they move is replaced by the prediction at the window's end
-            if (K / f > 1 && (rc = swe_run_steps(h, K / f - 1)) != SWE_OK) break;
+            if (K / f > 2 && (rc = swe_run_steps(h, K / f - 2)) != SWE_OK) break;
             if ((rc = swe_get_time(h, &t1)) != SWE_OK) break;
             if (!couple(s, h, k) || (rc = after_solver(s, k)) != SWE_OK) { rc = rc == SWE_OK ? SWE_EINVAL : rc; break; }
             if ((rc = check_err(s)) != SWE_OK || (rc = launch_apply(s, h, k)) != SWE_OK) break;

@@ -57,9 +57,11 @@ struct swe_handle {
     int diag_blocks = 0;
     void *allocs[32] = {};
     int nalloc = 0;
-    cudaGraphExec_t graph = nullptr;    // the graph for the current coupling (one of gcache)
-    cudaGraphExec_t gcache[2] = {};     // by sediment_on
+    cudaGraphExec_t graph = nullptr;    // the graph in use (one of gcache)
+    cudaGraphExec_t gcache[2][2] = {};  // by sediment_on, by launch (dense, sparse)
     int graph_steps = 0;
+    int sparse_grid = 0;                // CUDA blocks of a sparse step (about one wave)
+    int *h_hint = nullptr;              // pinned: blocks computed by the last step of the last replay
     std::string err;
 };
 
@@ -92,8 +94,9 @@ static void dev_free(swe_handle *h, void *p) {
 
 // ---------------------------------------------------------------- launchers
 
-static cudaError_t L_step(swe_handle *h) {
-    return is_f32(h) ? launch_step<float>(h->c, h->b, h->bw, h->stream) : launch_step<double>(h->c, h->b, h->bw, h->stream);
+static cudaError_t L_step(swe_handle *h, int grid) {
+    return is_f32(h) ? launch_step<float>(h->c, h->b, h->bw, h->stream, grid)
+                     : launch_step<double>(h->c, h->b, h->bw, h->stream, grid);
 }
 static cudaError_t L_between(swe_handle *h, int commit) {
     return is_f32(h) ? launch_between<float>(h->c, h->b, commit, h->stream)
@@ -105,8 +108,9 @@ static cudaError_t L_init(swe_handle *h) {
 static cudaError_t L_bed(swe_handle *h) {
     return is_f32(h) ? launch_bed_source<float>(h->c, h->b, h->stream) : launch_bed_source<double>(h->c, h->b, h->stream);
 }
-static cudaError_t L_one_step(swe_handle *h) {
-    cudaError_t e = L_step(h);
+// grid: 0 for a dense step, > 0 for a sparse one (see launch_step)
+static cudaError_t L_one_step(swe_handle *h, int grid = 0) {
+    cudaError_t e = L_step(h, grid);
     if (e == cudaSuccess && h->c.has_qb) e = L_bed(h);
     if (e == cudaSuccess) e = L_between(h, 1);
     return e;
@@ -186,6 +190,7 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     c.psi = p.psi; c.K = p.cfl_K; c.dt_max = p.dt_max; c.neg_tol = h->p.neg_tol;
     c.eps_f = float_floor_of(p.eps_wet);
     swe_fill_f32(c);
+    swe_set_regions(c);
 
     SweBufs &b = h->b;
     size_t ntiles = (size_t)c.tiles_x * c.tiles_y;
@@ -194,6 +199,14 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = dev_alloc(h, (void **)&b.census[q], ntiles * sizeof(int));
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.skipped, ntiles);
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.work, (ntiles + 2) * sizeof(int));
+    const size_t nreg = (size_t)c.regions_x * c.regions_y;
+    if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.rcen, nreg * sizeof(int));
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = dev_alloc(h, (void **)&b.rneed[q], nreg);
+    {   // a sparse step launches about one wave of the step kernel (two blocks per SM)
+        int sms = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        h->sparse_grid = 2 * (sms > 0 ? sms : 1);
+    }
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.dev, sizeof(SweDev));
     h->diag_blocks = (int)std::min<long long>(1024, (ncell + 255) / 256);
     if (e == cudaSuccess) e = dev_alloc(h, (void **)&b.partials, sizeof(double) * 3 * h->diag_blocks);
@@ -204,6 +217,8 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
     b.src_rowptr = rowptr;
     b.src_x = nullptr;
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_dev, sizeof(SweDev));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_hint, sizeof(int));
+    if (e == cudaSuccess) *h->h_hint = (int)ntiles;
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_diag, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.dev, 0, sizeof(SweDev), h->stream);
     if (e != cudaSuccess) {
@@ -221,8 +236,9 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
 // Step graphs are captured per coupling mode (Exner on / off) and dropped
 // whenever anything they bake in (parameters, buffers, tiling) changes.
 static void drop_graphs(swe_handle *h) {
-    for (cudaGraphExec_t &g : h->gcache)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &gs : h->gcache)
+        for (cudaGraphExec_t &g : gs)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     h->graph = nullptr;
 }
 
@@ -232,6 +248,7 @@ extern "C" swe_status swe_destroy(swe_handle *h) {
     drop_graphs(h);
     for (int i = 0; i < h->nalloc; ++i) cudaFree(h->allocs[i]);
     if (h->h_dev) cudaFreeHost(h->h_dev);
+    if (h->h_hint) cudaFreeHost(h->h_hint);
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -441,6 +458,7 @@ extern "C" swe_status swe_set_state_ex(swe_handle *h, const void *H, const void 
     swe_status s = read_dev(h);
     if (s != SWE_OK) return s;
     h->state_set = true;
+    *h->h_hint = h->c.tiles_x * h->c.tiles_y;   // unknown activity: dense launches until a step tells
     h->tend_active = false;
     return check_status(h);
 }
@@ -495,22 +513,35 @@ static swe_status free_stepping(swe_handle *h) {
     return SWE_OK;
 }
 
-static swe_status ensure_graph(swe_handle *h) {
-    h->graph = h->gcache[h->c.sediment_on ? 1 : 0];
+// Launch of the next steps: sparse (a wave of CUDA blocks walking the block
+// list) while the blocks computed by the last known step fit in it, dense
+// (one CUDA block per grid block) otherwise.  Results are the same either
+// way; only the launch differs.
+static int step_grid(const swe_handle *h, int active) {
+    return (h->c.hgs && active >= 0 && active <= h->sparse_grid) ? h->sparse_grid : 0;
+}
+
+// The step graph of the current coupling and launch kind; each replay ends by
+// copying the blocks computed by its last step into the pinned hint.
+static swe_status ensure_graph(swe_handle *h, bool sparse) {
+    cudaGraphExec_t &slot = h->gcache[h->c.sediment_on ? 1 : 0][sparse ? 1 : 0];
+    h->graph = slot;
     if (h->graph) return SWE_OK;
     long long ncell = (long long)h->c.nx * h->c.ny;
     int m = ncell >= (1ll << 24) ? 8 : (ncell >= (1ll << 20) ? 32 : 128);
     cudaGraph_t g;
     CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < m && e == cudaSuccess; ++i) e = L_one_step(h);
+    for (int i = 0; i < m && e == cudaSuccess; ++i) e = L_one_step(h, sparse ? h->sparse_grid : 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->h_hint, &h->b.dev->active_last, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(h, SWE_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, SWE_ECUDA, std::string("capture end: ") + cudaGetErrorString(e2));
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->graph = nullptr; return fail(h, SWE_ECUDA, cudaGetErrorString(e)); }
-    h->gcache[h->c.sediment_on ? 1 : 0] = h->graph;
+    slot = h->graph;
     h->graph_steps = m;
     return SWE_OK;
 }
@@ -521,9 +552,10 @@ extern "C" swe_status swe_step(swe_handle *h, double *dt_taken) {
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_step before swe_set_state");
     swe_status s = free_stepping(h);
     if (s != SWE_OK) return s;
-    CU(h, L_one_step(h));
+    CU(h, L_one_step(h, step_grid(h, *h->h_hint)));
     s = read_dev(h);
     if (s != SWE_OK) return s;
+    *h->h_hint = h->h_dev->active_last;
     if (dt_taken) *dt_taken = h->h_dev->dt_last;
     return check_status(h);
 }
@@ -534,14 +566,17 @@ extern "C" swe_status swe_run_steps(swe_handle *h, int64_t nsteps) {
     if (!h->state_set) return fail(h, SWE_ESTATE, "swe_run_steps before swe_set_state");
     swe_status s = free_stepping(h);
     if (s != SWE_OK) return s;
-    s = ensure_graph(h);
+    // the hint is what the last replay left in pinned memory (possibly an older
+    // replay's if the last one is still running): it only picks the launch
+    const int grid = step_grid(h, *h->h_hint);
+    s = ensure_graph(h, grid > 0);
     if (s != SWE_OK) return s;
     int64_t left = nsteps;
     while (left >= h->graph_steps) {
         CU(h, cudaGraphLaunch(h->graph, h->stream));
         left -= h->graph_steps;
     }
-    for (; left > 0; --left) CU(h, L_one_step(h));
+    for (; left > 0; --left) CU(h, L_one_step(h, grid));
     return SWE_OK;
 }
 
@@ -556,13 +591,14 @@ extern "C" swe_status swe_advance(swe_handle *h, double t_end, int64_t *steps_ta
     CU(h, cudaGetLastError());
     CU(h, L_between(h, 0));
     h->tend_active = true;
-    s = ensure_graph(h);
-    if (s != SWE_OK) return s;
     for (;;) {
         s = read_dev(h);
         if (s != SWE_OK) return s;
         if (h->h_dev->status) break;
         if (h->h_dev->done || !h->h_dev->scheduled) break;
+        if (h->h_dev->n != n0) *h->h_hint = h->h_dev->active_last;
+        s = ensure_graph(h, step_grid(h, *h->h_hint) > 0);
+        if (s != SWE_OK) return s;
         CU(h, cudaGraphLaunch(h->graph, h->stream));
     }
     if (steps_taken) *steps_taken = h->h_dev->n - n0;
@@ -677,7 +713,18 @@ void *handle_current_state(swe_handle *h) {
 int handle_state_changed(swe_handle *h) {
     if (!h) return SWE_EINVAL;
     const size_t nt = (size_t)h->c.tiles_x * h->c.tiles_y;
-    return cudaMemsetAsync(h->b.skipped, 0, nt, h->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
+    // every block's buffers may differ, and the region census is stale (the
+    // next compaction rebuilds it: rescan's low byte set, the others are 0)
+    if (cudaMemsetAsync(h->b.skipped, 0, nt, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(&h->b.dev->rescan, 1, 1, h->stream) != cudaSuccess)
+        return SWE_ECUDA;
+    *h->h_hint = (int)nt;
+    return SWE_OK;
+}
+
+int handle_regions_stale(swe_handle *h) {
+    if (!h) return SWE_EINVAL;
+    return cudaMemsetAsync(&h->b.dev->rescan, 1, 1, h->stream) == cudaSuccess ? SWE_OK : SWE_ECUDA;
 }
 
 int handle_retile(swe_handle *h, int bw, int th) {
@@ -687,17 +734,27 @@ int handle_retile(swe_handle *h, int bw, int th) {
     const int tw = bw - 8;
     const int tx = (c.nx + tw - 1) / tw, ty = (c.ny + th - 1) / th;
     const size_t nt = (size_t)tx * ty;
+    const size_t nreg = (size_t)((tx + SWE_REGION - 1) / SWE_REGION) * ((ty + SWE_REGION - 1) / SWE_REGION);
     void *cen0 = nullptr, *cen1 = nullptr, *skp = nullptr, *wrk = nullptr;
+    void *rc0 = nullptr, *rn0 = nullptr, *rn1 = nullptr;
     if (dev_alloc(h, &cen0, nt * sizeof(int)) != cudaSuccess || dev_alloc(h, &cen1, nt * sizeof(int)) != cudaSuccess ||
-        dev_alloc(h, &skp, nt) != cudaSuccess || dev_alloc(h, &wrk, (nt + 2) * sizeof(int)) != cudaSuccess) {
+        dev_alloc(h, &skp, nt) != cudaSuccess || dev_alloc(h, &wrk, (nt + 2) * sizeof(int)) != cudaSuccess ||
+        dev_alloc(h, &rc0, nreg * sizeof(int)) != cudaSuccess ||
+        dev_alloc(h, &rn0, nreg) != cudaSuccess || dev_alloc(h, &rn1, nreg) != cudaSuccess) {
         dev_free(h, cen0); dev_free(h, cen1); dev_free(h, skp); dev_free(h, wrk);
+        dev_free(h, rc0); dev_free(h, rn0); dev_free(h, rn1);
         return SWE_ENOMEM;
     }
     dev_free(h, h->b.census[0]); dev_free(h, h->b.census[1]); dev_free(h, h->b.skipped); dev_free(h, h->b.work);
+    dev_free(h, h->b.rcen); dev_free(h, h->b.rneed[0]); dev_free(h, h->b.rneed[1]);
     h->b.census[0] = (int *)cen0; h->b.census[1] = (int *)cen1; h->b.skipped = (unsigned char *)skp;
     h->b.work = (int *)wrk;
+    h->b.rcen = (int *)rc0;
+    h->b.rneed[0] = (unsigned char *)rn0; h->b.rneed[1] = (unsigned char *)rn1;
     h->bw = bw;
     c.tw = tw; c.th = th; c.tiles_x = tx; c.tiles_y = ty;
+    swe_set_regions(c);
+    *h->h_hint = (int)nt;
     drop_graphs(h);
     if (!h->state_set) return SWE_OK;
     // census of the current state (its buffer is buf[n & 1]); the maxima the

@@ -4,14 +4,21 @@
 //
 // Each scenario is an ordinary solver handle (swe_create): its state, Manning
 // field, sources and diagnostics are set and read with the usual calls.  The
-// persistent kernel walks a flattened list of (scenario, block) work items:
-//   for each step: every block takes work items round-robin and runs the
-//   same per-block step as the single-grid kernel (K1 skip, K2-K8, census and
-//   Eq. 7 maxima); grid barrier; one thread per scenario forms that
-//   scenario's next dt (its own K3; scenarios keep their own time); barrier.
-// The grid barrier spins with a time limit: if it runs out the kernel sets a
-// status bit and returns, so the host reads SWE_ETIMEOUT and the context stays
-// usable.  The cooperative launch guarantees all blocks are co-resident.
+// persistent kernel schedules a flattened list of (scenario, block) work
+// items by dataflow, with no grid-wide barrier:
+//   * blocks draw (step, item) pairs in order from one counter, step-major;
+//   * an item of scenario k at step n waits (bounded) until scenario k has
+//     completed n steps in this launch -- other scenarios never hold it up,
+//     since each keeps its own dt (its own K3) and time;
+//   * each item runs the same per-block step as the single-grid kernel (K1
+//     skip, K2-K8, census and Eq. 7 maxima) and counts itself done; the block
+//     that completes scenario k's step commits it and forms k's next dt, then
+//     publishes the step count.
+// Items are drawn in increasing order and an item only waits for items drawn
+// before it, so the earliest unfinished item can always run: the schedule
+// cannot deadlock.  Every wait polls %globaltimer with a time limit; on expiry
+// the kernel sets a status bit, every block returns, the host reads
+// SWE_ETIMEOUT, and the context stays usable.
 //
 // An autotuner (swe_ensemble_autotune) times each candidate block shape on
 // the ensemble's own states and keeps the fastest.
@@ -39,70 +46,70 @@ __device__ inline unsigned long long global_ns() {
     return t;
 }
 
-// Sense-counting grid barrier over `expected` blocks with a time limit.
-// bar[0] counts arrivals, bar[1] is the generation.  Returns false (and sets
-// the timeout status bit) if the other blocks did not arrive in time.
-__device__ bool grid_sync(unsigned *bar, unsigned expected, unsigned long long timeout_ns, unsigned *status) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        int ok = 1;
-        if (arrived == expected - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*vgen == gen) {
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicOr(status, SWE_STATUS_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        if (*(volatile unsigned *)status & SWE_STATUS_TIMEOUT) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
+// Layout of the launch's synchronisation words (zeroed before every launch):
+// [0] the (step, item) counter, [1] unused, [2] status, then per scenario k
+// done[k] = ENS_SYNC + 2k (items of its current step completed) and
+// steps[k] = ENS_SYNC + 2k + 1 (steps completed in this launch).
+#define ENS_SYNC 4
 
 // GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; the
-// sources are always compiled in (scenarios carry inflow).
+// sources are always compiled in (scenarios carry inflow).  extra: completions
+// each scenario step waits for beyond its items (0; > 0 only to make the waits
+// run out in a test).
 template <int BW, bool GEN>
 __global__ void __launch_bounds__(BW, 2)
-ensemble_kernel(const EnsScen *__restrict__ scen, int nscen, const int4 *__restrict__ items, int nitems,
-                int nsteps, unsigned *bar, unsigned expected, unsigned *status, unsigned long long timeout_ns,
-                unsigned *ctr) {
+ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items, int nitems, int nsteps,
+                unsigned *sync, unsigned extra, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
-    __shared__ int s_it;
-    for (int step = 0; step < nsteps; ++step) {
-        // work items taken in order from a counter (ctr[step parity], zero at
-        // the step's start): a block that drew cheap (dry) items takes more
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) s_it = (int)atomicAdd(ctr + (step & 1), 1u);
-            __syncthreads();
-            const int it = s_it;
-            if (it >= nitems) break;
-            const int4 w = items[it];
-            step_tile<float, BW, true, true, GEN>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
+    __shared__ long long s_g;
+    __shared__ int s_stop;
+    volatile unsigned *vsync = sync;
+    const long long total = (long long)nsteps * nitems;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_g = (vsync[2] & SWE_STATUS_TIMEOUT) ? total : (long long)atomicAdd(sync, 1u);
+            s_stop = 0;
         }
-        if (!grid_sync(bar, expected, timeout_ns, status)) return;
-        if (blockIdx.x == 0) {
-            for (int k = threadIdx.x; k < nscen; k += BW) between_body<float>(scen[k].c, scen[k].B, 1);
-            // the next step's counter: its last use ended before the barrier above
-            if (threadIdx.x == 0) atomicExch(ctr + ((step + 1) & 1), 0u);
+        __syncthreads();
+        const long long g = s_g;
+        if (g >= total) return;
+        const int step = (int)(g / nitems);
+        const int4 w = items[g % nitems];
+        // wait until scenario w.x has completed `step` steps of this launch
+        if (threadIdx.x == 0) {
+            volatile unsigned *done_steps = vsync + ENS_SYNC + 2 * w.x + 1;
+            if (*done_steps < (unsigned)step) {
+                const unsigned long long t0 = global_ns();
+                while (*done_steps < (unsigned)step) {
+                    if ((vsync[2] & SWE_STATUS_TIMEOUT) || global_ns() - t0 > timeout_ns) {
+                        atomicOr(sync + 2, SWE_STATUS_TIMEOUT);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
         }
-        if (!grid_sync(bar, expected, timeout_ns, status)) return;
+        __syncthreads();
+        if (s_stop) return;
+        const EnsScen &sc = scen[w.x];
+        step_tile<float, BW, true, true, GEN>(sc.c, sc.B, w.y, w.z, S);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();   // this item's state, census and maxima before its count
+            const unsigned target = (unsigned)(sc.c.tiles_x * sc.c.tiles_y) + extra;
+            if (atomicAdd(sync + ENS_SYNC + 2 * w.x, 1u) + 1u == target) {
+                // the scenario's step is complete: commit it, form its next dt
+                atomicExch(sync + ENS_SYNC + 2 * w.x, 0u);
+                __threadfence();
+                between_body<float>(sc.c, sc.B, 1);
+                __threadfence();
+                atomicExch(sync + ENS_SYNC + 2 * w.x + 1, (unsigned)(step + 1));
+            }
+        }
     }
 }
 
@@ -116,14 +123,14 @@ struct swe_ensemble {
     EnsScen *d_scen = nullptr;
     int4 *d_items = nullptr;
     size_t items_cap = 0;
-    unsigned *d_bar = nullptr;   // [0] arrivals, [1] generation, [2] status, [3..4] work counters
+    unsigned *d_sync = nullptr;  // ENS_SYNC + 2 n words: work counter, status, per-scenario counts
     unsigned long long timeout_ns = 2000000000ull;
-    int extra_arrivals = 0;
+    int extra = 0;            // test hook: completions each scenario step waits for beyond its items
     std::map<long long, cudaGraphExec_t> graphs;
     int nitems = 0;
     int grid = 0;            // co-resident blocks of the persistent kernel for bw
     bool gen = false;        // some scenario uses the general transport laws
-    bool graph_ok = true;    // false if this driver cannot capture the cooperative launch
+    bool graph_ok = true;    // false if this driver cannot capture the persistent launch
 };
 
 namespace {
@@ -180,24 +187,19 @@ swe_status upload(swe_ensemble *e) {
 template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
     const int grid = e->grid;
     const size_t smem = sizeof(StepSmem<float, BW>);
-    cudaError_t err = cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned), e->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(e->d_bar + 3, 0, 2 * sizeof(unsigned), e->stream);
+    const size_t words = ENS_SYNC + 2 * e->members.size();
+    cudaError_t err = cudaMemsetAsync(e->d_sync, 0, words * sizeof(unsigned), e->stream);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(BW);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = e->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 0;   // no grid barrier: blocks need not be co-resident
     const EnsScen *sc = e->d_scen;
     const int4 *it = e->d_items;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN>, sc, (int)e->members.size(), it, e->nitems, nsteps,
-                              e->d_bar, (unsigned)(grid + e->extra_arrivals), e->d_bar + 2, e->timeout_ns,
-                              e->d_bar + 3);
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN>, sc, it, e->nitems, nsteps, e->d_sync,
+                              (unsigned)e->extra, e->timeout_ns);
 }
 
 cudaError_t launch_any(swe_ensemble *e, int nsteps) {
@@ -229,12 +231,12 @@ swe_status graph_for(swe_ensemble *e, int nsteps, cudaGraphExec_t *out) {
 
 swe_status check(swe_ensemble *e) {
     unsigned st = 0;
-    if (cudaMemcpyAsync(&st, e->d_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, e->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(&st, e->d_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, e->stream) != cudaSuccess ||
         cudaStreamSynchronize(e->stream) != cudaSuccess)
         return SWE_ECUDA;
     if (st & SWE_STATUS_TIMEOUT) {
         // clear the bit so the ensemble can be used again once the cause is fixed
-        cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream);
+        cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * e->members.size()) * sizeof(unsigned), e->stream);
         cudaStreamSynchronize(e->stream);
         return SWE_ETIMEOUT;
     }
@@ -274,8 +276,8 @@ extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void 
         e->members.push_back(h);
     }
     if (cudaMalloc(&e->d_scen, n * sizeof(EnsScen)) != cudaSuccess ||
-        cudaMalloc(&e->d_bar, 8 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream) != cudaSuccess) {
+        cudaMalloc(&e->d_sync, (ENS_SYNC + 2 * (size_t)n) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * (size_t)n) * sizeof(unsigned), e->stream) != cudaSuccess) {
         swe_ensemble_destroy(e);
         return SWE_ENOMEM;
     }
@@ -290,7 +292,7 @@ extern "C" swe_status swe_ensemble_destroy(swe_ensemble *e) {
     for (swe_handle *h : e->members) swe_destroy(h);
     cudaFree(e->d_scen);
     cudaFree(e->d_items);
-    cudaFree(e->d_bar);
+    cudaFree(e->d_sync);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
     return SWE_OK;
@@ -311,9 +313,11 @@ extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
     if (e->grid == 0)
         e->grid = e->gen ? (e->bw == 128 ? resident_blocks<128, true>() : resident_blocks<256, true>())
                          : (e->bw == 128 ? resident_blocks<128, false>() : resident_blocks<256, false>());
-    // one persistent launch per call (split only beyond 2^30 steps)
+    // one persistent launch per call (split only where steps x items would
+    // overflow the 32-bit work counter)
+    const int64_t max_chunk = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max(1, e->nitems));
     while (nsteps > 0) {
-        const int chunk = (int)std::min<int64_t>(nsteps, 1 << 30);
+        const int chunk = (int)std::min<int64_t>(nsteps, max_chunk);
         cudaGraphExec_t g;
         if (e->graph_ok && graph_for(e, chunk, &g) == SWE_OK) {
             if (cudaGraphLaunch(g, e->stream) != cudaSuccess) return SWE_ECUDA;
@@ -322,15 +326,18 @@ extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
         }
         nsteps -= chunk;
     }
+    for (swe_handle *h : e->members)
+        if (handle_regions_stale(h) != SWE_OK) return SWE_ECUDA;
     return check(e);
 }
 
 extern "C" swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, int extra_arrivals) {
     if (!e || !(seconds > 0) || extra_arrivals < 0) return SWE_EINVAL;
     e->timeout_ns = (unsigned long long)(seconds * 1e9);
-    e->extra_arrivals = extra_arrivals;
+    e->extra = extra_arrivals;
     clear_graphs(e);
-    if (cudaMemsetAsync(e->d_bar, 0, 8 * sizeof(unsigned), e->stream) != cudaSuccess) return SWE_ECUDA;
+    if (cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * e->members.size()) * sizeof(unsigned), e->stream) != cudaSuccess)
+        return SWE_ECUDA;
     return SWE_OK;
 }
 

@@ -28,6 +28,7 @@ struct SweDev {
     unsigned long long cells_copied;    // cells in blocks copied (skipped, buffers differed)
     unsigned long long acc[3];  // running maxima (bit patterns) of |v|, |v|+sqrt(gH), |J0|
     double vp, vs, jm;    // maxima of the current state, kept by `between`
+    int rescan;           // 1: the region census is stale; the next compaction rebuilds it and scans every block
 };
 
 // Model constants (plain data, passed by value).
@@ -35,6 +36,7 @@ struct SweConst {
     int nx, ny;
     int tw, th;             // HGS block: tw columns x th rows
     int tiles_x, tiles_y;
+    int regions_x, regions_y;  // HGS regions of SWE_REGION x SWE_REGION blocks
     int man_shift, man_w;   // Manning table: index (y >> shift) * man_w + (x >> shift)
     int sediment_on, aj_mode, m_is_2, hgs, literal_D, nk, has_qb;
     int nsrc;               // number of source cells
@@ -43,7 +45,9 @@ struct SweConst {
     int has_beta;           // per-cell infiltration rate present
     double g, dx, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, C_J, psi, K, dt_max, neg_tol;
     float eps_f;            // largest float <= eps: (float)H > eps_f <=> (double)H > eps
-    struct { float g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol; } f;  // the same, rounded to FP32
+    // the same, rounded to FP32; inv_dx = 1/h, inv_4dx = 1/(4h), inv_dxp = 1/(h (1-psi)): the step
+    // coefficients of the FP32 kernels are dt times these (ptxas can re-form them from dt)
+    struct { float g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol, inv_dx, inv_4dx, inv_dxp; } f;
 };
 
 // Fills the FP32 copies of the model constants.
@@ -51,6 +55,16 @@ inline void swe_fill_f32(SweConst &c) {
     c.f.g = (float)c.g; c.f.eps = (float)c.eps; c.f.coef = (float)c.coef; c.f.cjh = (float)c.cjh;
     c.f.ksh = (float)c.ksh; c.f.A_J = (float)c.A_J; c.f.m_exp = (float)c.m_exp; c.f.sm1 = (float)c.sm1;
     c.f.d50 = (float)c.d50; c.f.neg_tol = (float)c.neg_tol;
+    c.f.inv_dx = (float)(1.0 / c.dx); c.f.inv_4dx = (float)(1.0 / (4.0 * c.dx));
+    c.f.inv_dxp = (float)(1.0 / (c.dx * (1.0 - c.psi)));
+}
+
+// HGS region: SWE_REGION x SWE_REGION blocks (Sec. 3's second level above the blocks).
+#define SWE_REGION 8
+
+inline void swe_set_regions(SweConst &c) {
+    c.regions_x = (c.tiles_x + SWE_REGION - 1) / SWE_REGION;
+    c.regions_y = (c.tiles_y + SWE_REGION - 1) / SWE_REGION;
 }
 
 // Device pointers of one solver instance.
@@ -59,6 +73,8 @@ struct SweBufs {
     int *census[2];             // Index_block of K1 for state^n (census[n & 1])
     unsigned char *skipped;     // per block: 1 = both buffers equal on the block
     int *work;                  // blocks to run this step: [0] count, [1] unused, [2..] block indices
+    int *rcen;                  // HGS region census of the state being stepped: blocks with census > 0
+    unsigned char *rneed[2];    // per region: it or an edge neighbour held water in state^n (rneed[n & 1])
     const void *gn2;            // g n^2 table (element type = state type)
     const void *ajn;            // 0.05 n^3 table (Eq. 4 numerator)
     const int *src_rowptr;      // ny + 1 offsets into src_x
@@ -74,7 +90,9 @@ struct SweBufs {
 // Launchers implemented per precision (swe_f32.cu / swe_f64.cu).
 namespace swe_impl {
 template <typename T> size_t step_smem_bytes(int bw);
-template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s);
+// grid: 0 launches one CUDA block per grid block; > 0 launches at most that
+// many blocks, each walking the work list (for sparse steps)
+template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid = 0);
 template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s);
 template <typename T> cudaError_t launch_between(const SweConst &c, const SweBufs &b, int commit, cudaStream_t s);
 template <typename T> cudaError_t launch_diag(const SweConst &c, const SweBufs &b, int nblocks, cudaStream_t s);
@@ -99,6 +117,9 @@ void *handle_current_state(swe_handle *h);
 // The current state was modified outside the step kernels: forget which
 // dry blocks the ping-pong buffers agree on.
 int handle_state_changed(swe_handle *h);
+// The state was stepped by kernels that do not keep the HGS region census
+// (the ensemble's): the next compaction rebuilds it.
+int handle_regions_stale(swe_handle *h);
 }  // namespace swe_impl
 
 #define SWE_STATUS_TIMEOUT 4u   // device status bit: a bounded grid barrier gave up

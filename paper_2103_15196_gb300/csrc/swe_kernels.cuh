@@ -169,6 +169,7 @@ __device__ inline int ext_index(int i, int n, int lo_open, int hi_open, int &sgn
 template <typename T> struct K {  // step constants in the state precision
     T g, eps, coef, cjh, ksh, A_J, m_exp, sm1, d50, neg_tol;
     T dt, dtdx, hdt, c4, cb, dHs;
+    T hdtc, dtc;  // FP32: dt/2 g/(2h) and dt g/(2h), the force terms' factors (unused in FP64)
 };
 
 // Grass discharge (Eq. 3) gated by the Shamov velocity (Eq. 5, written as
@@ -188,16 +189,16 @@ __device__ inline void grass(const SweConst &c, const K<T> &k, bool wet, T H, T 
     Ja = (AJ * vm) * mm_sqrt(s2);
 }
 
-// Pressure + bed-slope force per unit mass on one axis (K2 / K5):
-// -(g/2h) (eta_p' - eta_m') * ratio, ratio = stage depth / H^n (1 at t_n,
-// H^{n+1/2}/H^n = 1/A at the half step), where a dry neighbour whose bed is
-// at or above the cell's level counts as a wall (eta' = eta).
+// Free-surface difference eta_p' - eta_m' across a cell on one axis, for the
+// pressure + bed-slope force per unit mass -(g/2h) (eta_p' - eta_m') * ratio
+// (K2 / K5; ratio = stage depth / H^n: 1 at t_n, H^{n+1/2}/H^n = 1/A at the
+// half step), where a dry neighbour whose bed is at or above the cell's level
+// ec counts as a wall (eta' = ec).
 template <typename T>
-__device__ inline T axis_force(const K<T> &k, T ec, T ratio, T eta_p, T b_p, bool wet_p,
-                               T eta_m, T b_m, bool wet_m) {
+__device__ inline T axis_diff(T ec, T eta_p, T b_p, bool wet_p, T eta_m, T b_m, bool wet_m) {
     T ep = (!wet_p && b_p >= ec) ? ec : eta_p;
     T em = (!wet_m && b_m >= ec) ? ec : eta_m;
-    return -(k.coef * (ep - em)) * ratio;
+    return ep - em;
 }
 
 template <typename T> __device__ inline unsigned long long max_bits(T x);
@@ -296,6 +297,7 @@ template <> __device__ inline K<double> load_k<double>(const SweConst &c, const 
     k.A_J = c.A_J; k.m_exp = c.m_exp; k.sm1 = c.sm1; k.d50 = c.d50; k.neg_tol = c.neg_tol;
     const StepCoef r = step_coef(dev, coherent);
     k.dt = r.dt; k.dtdx = r.dtdx; k.hdt = r.hdt; k.c4 = r.c4; k.cb = r.cb; k.dHs = r.dHs;
+    k.hdtc = 0.0; k.dtc = 0.0;
     return k;
 }
 // FP32: the model constants come pre-rounded in the kernel parameters (so
@@ -305,8 +307,10 @@ template <> __device__ inline K<float> load_k<float>(const SweConst &c, const Sw
     k.g = c.f.g; k.eps = c.f.eps; k.coef = c.f.coef; k.cjh = c.f.cjh; k.ksh = c.f.ksh;
     k.A_J = c.f.A_J; k.m_exp = c.f.m_exp; k.sm1 = c.f.sm1; k.d50 = c.f.d50; k.neg_tol = c.f.neg_tol;
     const StepCoef r = step_coef(dev, coherent);
-    k.dt = (float)r.dt; k.dtdx = (float)r.dtdx; k.hdt = (float)r.hdt; k.c4 = (float)r.c4;
-    k.cb = (float)r.cb; k.dHs = (float)r.dHs;
+    k.dt = (float)r.dt;
+    k.dtdx = k.dt * c.f.inv_dx; k.hdt = 0.5f * k.dt; k.c4 = k.dt * c.f.inv_4dx;
+    k.cb = k.dt * c.f.inv_dxp; k.dHs = (float)r.dHs;
+    k.hdtc = k.hdt * c.f.coef; k.dtc = k.dt * c.f.coef;
     return k;
 }
 
@@ -323,25 +327,6 @@ __device__ inline int reflect(int i, int n, int lo_open, int hi_open, int &sgn) 
 // exp2/log2 power, a branch-free limiter and one reciprocal shared by the
 // three HLL fluxes.  FP64 (parity): IEEE division, cbrt and the oracle's
 // operation order.
-template <typename T> struct Ar;
-template <> struct Ar<double> {
-    __device__ static inline void div2(double a, double b, double d, double &x, double &y) { x = a / d; y = b / d; }
-    __device__ static inline double pow43(double x) { return x * cbrt(x); }
-    __device__ static inline double minmod(double a, double b) { return swe_impl::minmod(a, b); }
-};
-template <> struct Ar<float> {
-    __device__ static inline void div2(float a, float b, float d, float &x, float &y) {
-        const float r = 1.0f / d;
-        x = a * r; y = b * r;
-    }
-    __device__ static inline float pow43(float x) { return exp2f(1.33333333f * log2f(x)); }
-    // the median of (a, b, 0): 0 unless a and b share a sign, else the one
-    // nearer zero (four min/max, no branch)
-    __device__ static inline float minmod(float a, float b) {
-        return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
-    }
-};
-
 // HLL fluxes of mass and both momenta sharing the bounds sL <= sR.
 template <typename T>
 __device__ inline void hll3(T HL, T HR, T uL, T uR, T wxL, T wxR, T wyL, T wyR, T sL, T sR,
@@ -351,18 +336,93 @@ __device__ inline void hll3(T HL, T HR, T uL, T uR, T wxL, T wxR, T wyL, T wyR, 
     Fx = hll(UxL, UxR, UxL * uL, UxR * uR, sL, sR);
     Fy = hll(UyL, UyR, UyL * uL, UyR * uR, sL, sR);
 }
-template <>
-__device__ inline void hll3<float>(float HL, float HR, float uL, float uR, float wxL, float wxR, float wyL,
-                                   float wyR, float sL, float sR, float &Fm, float &Fx, float &Fy) {
-    const float UxL = HL * wxL, UxR = HR * wxR, UyL = HL * wyL, UyR = HR * wyR;
-    const float FmL = HL * uL, FmR = HR * uR, FxL = UxL * uL, FxR = UxR * uR, FyL = UyL * uL, FyR = UyR * uR;
-    if (sL >= 0.f) { Fm = FmL; Fx = FxL; Fy = FyL; return; }
-    if (sR <= 0.f) { Fm = FmR; Fx = FxR; Fy = FyR; return; }
-    const float inv = 1.0f / (sR - sL), ss = sL * sR;
-    Fm = ((sR * FmL - sL * FmR) + ss * (HR - HL)) * inv;
-    Fx = ((sR * FxL - sL * FxR) + ss * (UxR - UxL)) * inv;
-    Fy = ((sR * FyL - sL * FyR) + ss * (UyR - UyL)) * inv;
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+template <typename T> struct Ar;
+template <> struct Ar<double> {
+    __device__ static inline void div2(double a, double b, double d, double &x, double &y) { x = a / d; y = b / d; }
+    __device__ static inline double minmod(double a, double b) { return swe_impl::minmod(a, b); }
+    // Manning coefficient g n^2 / H^(4/3)
+    __device__ static inline double manning(double gn2, double H) { return gn2 / (H * cbrt(H)); }
+    // K4 particle depth H / A; the K5 depth ratio H^{n+1/2} / H^n
+    __device__ static inline double depth(double H, double A, double &iA) { iA = 0.0; return H / A; }
+    __device__ static inline double ratio(double hc, double Hc, double) { return hc / Hc; }
+    // K4 numerator v + dt/2 a^n and K6 numerator v + dt a^{n+1/2}, from the
+    // free-surface difference d, in the oracle's order of operations
+    __device__ static inline double k4_num(const K<double> &k, double u, double d) {
+        return u + k.hdt * (-(k.coef * d) * 1.0);
+    }
+    __device__ static inline double k6_factor(const K<double> &, double ratio) { return ratio; }
+    __device__ static inline double k6_num(const K<double> &k, double u, double d, double ratio) {
+        return u + k.dt * (-(k.coef * d) * ratio);
+    }
+    // HLL fluxes of one face from the hydrostatic face depths, the normal
+    // velocities and celerities, in the oracle's order of operations
+    __device__ static inline void hll_face(double HL, double HR, double uL, double uR, double cL, double cR,
+                                           double wxL, double wxR, double wyL, double wyR,
+                                           double &Fm, double &Fx, double &Fy) {
+        const double aL = uL - cL, aR = uR - cR, pL = uL + cL, pR = uR + cR;
+        const double sL = aL < aR ? aL : aR, sR = pL > pR ? pL : pR;
+        hll3<double>(HL, HR, uL, uR, wxL, wxR, wyL, wyR, sL, sR, Fm, Fx, Fy);
+    }
+};
+template <> struct Ar<float> {
+    __device__ static inline void div2(float a, float b, float d, float &x, float &y) {
+        const float r = 1.0f / d;
+        x = a * r; y = b * r;
+    }
+    // the median of (a, b, 0): 0 unless a and b share a sign, else the one
+    // nearer zero (four min/max, no branch)
+    __device__ static inline float minmod(float a, float b) {
+        return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
+    }
+    // g n^2 H^(-4/3) through exp2/log2 (no reciprocal)
+    __device__ static inline float manning(float gn2, float H) { return gn2 * exp2f(-1.33333333f * log2f(H)); }
+    // the reciprocal of A is kept: it is the K5 depth ratio of the same cell.
+    // Written as an explicit rcp.approx and a rounded product, so that no
+    // compiled copy of the sweep rewrites it (into a division, say) and the
+    // value carried to the next position is the one every copy would form.
+    __device__ static inline float depth(float H, float A, float &iA) {
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iA) : "f"(A));
+        return __fmul_rn(H, iA);
+    }
+    __device__ static inline float ratio(float, float, float iA) { return iA; }
+    // the same numerators with the constant factors folded: one FMA per axis
+    __device__ static inline float k4_num(const K<float> &k, float u, float d) { return fmaf(-k.hdtc, d, u); }
+    __device__ static inline float k6_factor(const K<float> &k, float ratio) { return k.dtc * ratio; }
+    __device__ static inline float k6_num(const K<float> &, float u, float d, float q) { return fmaf(-q, d, u); }
+    // HLL with the bounds clamped to sL <= 0 <= sR: the same flux in all three
+    // cases (sL >= 0 gives F_L, sR <= 0 gives F_R), so no branch.  With the
+    // advective fluxes F = U u it is F = U_L alpha + U_R beta,
+    // alpha = (sR uL - sL sR)/(sR - sL), beta = (sL sR - sL uR)/(sR - sL);
+    // mirrored states (a wall) give beta = -alpha exactly: zero mass flux.
+    // sL = sR = 0 only when both sides are at rest with no depth: zero flux.
+    __device__ static inline void hll_face(float HL, float HR, float uL, float uR, float cL, float cR,
+                                           float wxL, float wxR, float wyL, float wyR,
+                                           float &Fm, float &Fx, float &Fy) {
+        const float sL = min3f(uL - cL, uR - cR, 0.f);
+        const float sR = max3f(uL + cL, uR + cR, 0.f);
+        const float inv = 1.0f / fmaxf(sR - sL, 1e-30f);
+        const float a = sR * inv, bm = sL * inv, cc = a * sL;
+        const float al = fmaf(a, uL, -cc), be = fmaf(-bm, uR, cc);
+        // rounded products and sum written out: no contraction choice is left
+        // to the compiler, so every compiled copy of the sweep agrees bit for bit
+        const float P = __fmul_rn(HL, al), Q = __fmul_rn(HR, be);
+        Fm = __fadd_rn(P, Q);
+        Fx = fmaf(P, wxL, __fmul_rn(Q, wxR));
+        Fy = fmaf(P, wyL, __fmul_rn(Q, wyR));
+    }
+};
 
 // Face states of one cell along one axis from its two neighbours: limited
 // slope sigma = minmod(q - q_m, q_p - q); minus-side face value q - sigma/2,
@@ -386,12 +446,9 @@ __device__ inline void face_flux2(const SweConst &c, const K<T> &k, const T L[5]
     T HL = L[1] - bf, HR = R[1] - bf;
     if (!(HL > T(0))) HL = T(0);
     if (!(HR > T(0))) HR = T(0);
-    const T uL = L[2], uR = R[2];
     const T cL = wet_c ? mm_sqrt(k.g * HL) : T(0);
     const T cR = wet_e ? mm_sqrt(k.g * HR) : T(0);
-    const T aL = uL - cL, aR = uR - cR, pL = uL + cL, pR = uR + cR;
-    const T sL = aL < aR ? aL : aR, sR = pL > pR ? pL : pR;
-    hll3<T>(HL, HR, uL, uR, L[3], R[3], L[4], R[4], sL, sR, Fm, Fx, Fy);
+    Ar<T>::hll_face(HL, HR, L[2], R[2], cL, cR, L[3], R[3], L[4], R[4], Fm, Fx, Fy);
     Fj = T(0);
     if (c.sediment_on) {
         const T su = un_c + un_e;
@@ -400,12 +457,14 @@ __device__ inline void face_flux2(const SweConst &c, const K<T> &k, const T L[5]
     }
 }
 
-// Per-cell terms of Eq. 7 and the census for a new state value.
+// Per-cell terms of Eq. 7 and the census for a new state value.  cnt holds
+// the census count in its low 24 bits and the status bits from bit 24 (one
+// register for both).
 template <typename T, bool GEN = true>
 __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T hun, T hvn, T bn, T ajn,
-                                      bool src, int &cnt, T &m0, T &m1, T &m2, unsigned &st) {
+                                      bool src, unsigned &cnt, T &m0, T &m1, T &m2) {
     const bool wet = is_wet(hn, c);
-    cnt += (wet || src) ? 1 : 0;
+    cnt += (wet || src) ? 1u : 0u;
     if (wet) {
         T u, v;
         Ar<T>::div2(hun, hvn, hn, u, v);
@@ -417,8 +476,8 @@ __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T 
         grass<T, GEN>(c, k, true, hn, ajn, u, v, jx, jy, ja);
         m2 = ja > m2 ? ja : m2;
     }
-    if (!(hn >= -k.neg_tol)) st |= 2u;
-    if (!mm_finite(((hn + bn) + hun) + hvn)) st |= 1u;
+    if (!(hn >= -k.neg_tol)) cnt |= 2u << 24;
+    if (!mm_finite(((hn + bn) + hun) + hvn)) cnt |= 1u << 24;
 }
 
 // Shared-memory rings; each row is padded by 2 entries on both sides so the
@@ -463,11 +522,12 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
     bool out_lane;
     int gn2_row, aj_row;
     T gn2, ajo, aj_out;
-    T qE[5], qN[5], G1[4], G2[4];
+    T qE[5], qN[5];
+    T G1[4], dG[4];         // the last y-face fluxes, and their difference to the ones before (K8's y term)
     T vA[2], vB[2];         // own-column v^n of rows s-P, s-P+1 and of the two rows before
-    int cnt;
+    T iA[2];                // own-column 1/A of K4 (FP32), by the parity of the position that formed it
+    unsigned cnt;           // census count (low 24 bits) | status bits << 24
     T m0, m1, m2;
-    unsigned st;
     T aH, aHu, aHv, ab, bH, bHu, bHv, bb0;
     int asy, bsy;
     V2<T> *hbk[4];          // 2-row banks of the 8-row (H, b) ring holding rows 2m-2j, 2m-2j+1
@@ -527,7 +587,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
         // ---------------- K4 (part): particle depth at t_{n+1/2}, row s-1
         if (FULL || (s - 1 >= y0 - 3 && s - 1 <= y1 + 2)) {
             const T A = T(1) + k.c4 * ((q4<P, 1>(S.u)[o + 1] - q4<P, 1>(S.u)[o - 1]) + (v_s - vB[P]));
-            q4<P, 1>(S.hj)[o].x = HB<P, 1>()[o].x / A;
+            q4<P, 1>(S.hj)[o].x = Ar<T>::depth(HB<P, 1>()[o].x, A, iA[P]);
         }
         // ---------------- K2, K4, K5, K6 and Grass load, row s-2
         if (FULL || (s - 2 >= y0 - 2 && s - 2 <= y1 + 1)) {
@@ -549,26 +609,26 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 const V2<T> N = HB<P, 1>()[o], Sc = HB<P, 3>()[o];
                 const T HE = E.x, bE = E.y, HW = Wc.x, bW = Wc.y, HN = N.x, bN = N.y, HS = Sc.x, bS = Sc.y;
                 const bool wE = is_wet(HE, c), wW = is_wet(HW, c), wN = is_wet(HN, c), wS = is_wet(HS, c);
-                // K2: forces at t_n
+                // K2: forces at t_n (free-surface differences per axis)
                 const T ec = Hc + bc;
-                const T ax = axis_force<T>(k, ec, T(1), HE + bE, bE, wE, HW + bW, bW, wW);
-                const T ay = axis_force<T>(k, ec, T(1), HN + bN, bN, wN, HS + bS, bS, wS);
+                const T dx2 = axis_diff<T>(ec, HE + bE, bE, wE, HW + bW, bW, wW);
+                const T dy2 = axis_diff<T>(ec, HN + bN, bN, wN, HS + bS, bS, wS);
                 // K4: predictor velocity, point-implicit Manning at |v^n|
-                const T cf = gn2 / Ar<T>::pow43(Hc);
+                const T cf = Ar<T>::manning(gn2, Hc);
                 const T va = mm_sqrt(u * u + v * v);
                 const T den = T(1) + k.hdt * (cf * va);
-                Ar<T>::div2(u + k.hdt * ax, v + k.hdt * ay, den, vtx, vty);
+                Ar<T>::div2(Ar<T>::k4_num(k, u, dx2), Ar<T>::k4_num(k, v, dy2), den, vtx, vty);
                 // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
                 const T hc = q4<P, 2>(S.hj)[o].x, ech = hc + bc;
                 const T hE = q4<P, 2>(S.hj)[o + 1].x, hW = q4<P, 2>(S.hj)[o - 1].x;
                 const T hN = q4<P, 1>(S.hj)[o].x, hS = q4<P, 3>(S.hj)[o].x;
-                const T ratio = hc / Hc;
-                const T bxf = axis_force<T>(k, ech, ratio, hE + bE, bE, wE, hW + bW, bW, wW);
-                const T byf = axis_force<T>(k, ech, ratio, hN + bN, bN, wN, hS + bS, bS, wS);
+                const T q = Ar<T>::k6_factor(k, Ar<T>::ratio(hc, Hc, iA[P ^ 1]));
+                const T dx5 = axis_diff<T>(ech, hE + bE, bE, wE, hW + bW, bW, wW);
+                const T dy5 = axis_diff<T>(ech, hN + bN, bN, wN, hS + bS, bS, wS);
                 // K6: corrector (Lagrangian end) velocity, Manning at |vt|
                 const T vat = mm_sqrt(vtx * vtx + vty * vty);
                 const T den2 = T(1) + k.dt * (cf * vat);
-                Ar<T>::div2(u + k.dt * bxf, v + k.dt * byf, den2, wxv, wyv);
+                Ar<T>::div2(Ar<T>::k6_num(k, u, dx5, q), Ar<T>::k6_num(k, v, dy5, q), den2, wxv, wyv);
                 grass<T, GEN>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
             q4<P, 2>(S.U)[o] = V2<T>{vtx, vty};
@@ -587,12 +647,12 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                     if (SWE_IN(q, c.nsrc)) src |= (B.src_x[q] == x);
             const V4<T> f = S.xf[PM5_2][o], fw = S.xf[PM5_2][o - 1];
             const V2<T> w = q4<P, 5>(S.W)[o];
-            T hn = Hc - k.dtdx * ((f.a - fw.a) + (G1[0] - G2[0]));
+            T hn = Hc - k.dtdx * ((f.a - fw.a) + dG[0]);
             if (src) hn = hn + k.dHs;
             if (SRC && c.has_rain && SWE_IN((long long)r * c.nx + x, SWE_NCELL))
                 hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
-            T hun = Hc * w.x - k.dtdx * ((f.b - fw.b) + (G1[1] - G2[1]));
-            T hvn = Hc * w.y - k.dtdx * ((f.c - fw.c) + (G1[2] - G2[2]));
+            T hun = Hc * w.x - k.dtdx * ((f.b - fw.b) + dG[1]);
+            T hvn = Hc * w.y - k.dtdx * ((f.c - fw.c) + dG[2]);
             if (SRC && c.has_beta && SWE_IN((long long)r * c.nx + x, SWE_NCELL)) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
@@ -605,13 +665,13 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
                 }
             }
             if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
-            const T bn = bc - k.cb * ((f.d - fw.d) + (G1[3] - G2[3]));
+            const T bn = bc - k.cb * ((f.d - fw.d) + dG[3]);
             if (SWE_IN((long long)r * c.nx + x, SWE_NCELL)) CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
             if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row && SWE_IN((r >> c.man_shift) * c.man_w + mcol, SWE_NMAN)) {
                 aj_row = r >> c.man_shift;
                 aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
             }
-            cell_epilogue2<T, GEN>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, st);
+            cell_epilogue2<T, GEN>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2);
         }
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
@@ -668,7 +728,7 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             }
             if (FULL || s - 3 >= y0) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { G2[q] = G1[q]; G1[q] = G[q]; }
+                for (int q = 0; q < 4; ++q) { dG[q] = G[q] - G1[q]; G1[q] = G[q]; }
             }
         }
         __syncthreads();
@@ -707,8 +767,10 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
         };
         bool active = cen(tile) > 0 || cen(by * c.tiles_x + l) > 0 || cen(by * c.tiles_x + r) > 0 ||
                       cen(d * c.tiles_x + bx) > 0 || cen(u * c.tiles_x + bx) > 0;
+        // the skip flag was written by whichever block ran this tile last
+        const bool was_skipped = COHERENT ? __ldcg(B.skipped + tile) != 0 : B.skipped[tile] != 0;
         if (!active) {
-            if (!B.skipped[tile]) {
+            if (!was_skipped) {
                 int x1 = min(tx0 + c.tw, c.nx);
                 for (int y = y0; y < y1; ++y)
                     for (int x = tx0 + t; x < x1; x += BW) {
@@ -718,7 +780,7 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
                     }
             }
             if (t == 0) {
-                if (!B.skipped[tile])
+                if (!was_skipped)
                     atomicAdd(&dev->cells_copied, (unsigned long long)(min(tx0 + c.tw, c.nx) - tx0) * (y1 - y0));
                 cen_out[tile] = 0;
                 B.skipped[tile] = 1;
@@ -746,9 +808,10 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
 #pragma unroll
     for (int q = 0; q < 5; ++q) { w.qE[q] = T(0); w.qN[q] = T(0); }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.G2[q] = T(0); }
+    for (int q = 0; q < 4; ++q) { w.G1[q] = T(0); w.dG[q] = T(0); }
     w.vA[0] = w.vA[1] = T(0);
-    w.cnt = 0; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0); w.st = 0;
+    w.iA[0] = w.iA[1] = T(0);
+    w.cnt = 0u; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0);
     {
         int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
         if (SWE_IN((long long)yy * c.nx + w.xx, SWE_NCELL)) w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
@@ -766,76 +829,149 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
             w.template pos<1, false>(s + 1);
         }
     }
-    block_finish<T, BW>(w.cnt, w.m0, w.m1, w.m2, w.st, tile, cen_out, dev, 1);
+    block_finish<T, BW>((int)(w.cnt & 0xffffffu), w.m0, w.m1, w.m2, w.cnt >> 24, tile, cen_out, dev, 1);
 }
 
-// The blocks the next step must run (HGS region of K1, Sec. 3, compacted):
-// those active by the K1 rule (the block or one of its four edge neighbours
-// holds water or a source) and dry ones whose two state buffers still
-// differ (one copy carries them over).  Written in block order to work[2..],
-// with the count in work[0] (work[1] is not used).  The
-// census of the next state is 0 for every block left out (it stays dry), so
-// it is written here for them.  Without the dry-block skip every block is
-// listed.  One block of 1024 threads (T: the state type, for one instance
-// per precision's translation unit).
+// The blocks the next step must run (HGS, Sec. 3: regions of SWE_REGION x
+// SWE_REGION blocks above the blocks, compacted): those active by the K1 rule
+// (the block or one of its four edge neighbours holds water or a source) and
+// dry ones whose two state buffers still differ (one copy carries them over).
+// Only the blocks of regions that hold water, or border one that does, in
+// the current state or the previous one are examined: a block elsewhere is
+// dry with dry neighbours, was carried over already, and has census 0 in the
+// buffer the next census goes to.  The region census of the state (blocks
+// with census > 0) is counted over the previous step's list, the only blocks
+// whose census can be > 0; when that list is stale (after a state is set or
+// changed outside the step) it is counted over every block and every block is
+// examined.  The list goes to work[2..] with the count
+// in work[0]; the census of the next state is written as 0 for every examined
+// block left out.  Without the dry-block skip every block is listed.  One
+// block of 1024 threads (T: the state type, for one instance per precision's
+// translation unit).
 template <typename T>
 __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
     __shared__ int wsum[32];
-    __shared__ int base, chunk;
+    __shared__ int base, chunk, nscan;
+    __shared__ int rlist[1024];
     const long long n = B.dev->n;
-    const int *cen = (n & 1) ? B.census[1] : B.census[0];
-    int *cen_next = (n & 1) ? B.census[0] : B.census[1];
+    const int par = (int)(n & 1);
+    const int *cen = par ? B.census[1] : B.census[0];
+    int *cen_next = par ? B.census[0] : B.census[1];
     const int nt = c.tiles_x * c.tiles_y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    for (int t0 = 0; t0 < nt; t0 += 1024) {
-        const int tile = t0 + (int)threadIdx.x;
-        bool need = false;
-        if (tile < nt) {
-            need = true;
-            if (c.hgs) {
-                const int bx = tile % c.tiles_x, by = tile / c.tiles_x;
-                const int l = bx > 0 ? bx - 1 : bx, r = bx < c.tiles_x - 1 ? bx + 1 : bx;
-                const int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
-                const bool active = cen[tile] > 0 || cen[by * c.tiles_x + l] > 0 || cen[by * c.tiles_x + r] > 0 ||
-                                    cen[d * c.tiles_x + bx] > 0 || cen[u * c.tiles_x + bx] > 0;
-                need = active || !B.skipped[tile];
-                if (!need) cen_next[tile] = 0;
-            }
+    if (!c.hgs) {   // every block, in order; the region census is not kept meanwhile
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += 1024) B.work[2 + t] = t;
+        if (threadIdx.x == 0) {
+            B.work[0] = nt;
+            B.dev->rescan = 1;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, need);
+        return;
+    }
+    const int nreg = c.regions_x * c.regions_y;
+    int *rc = B.rcen;
+    unsigned char *rn = par ? B.rneed[1] : B.rneed[0];
+    const unsigned char *rn_prev = par ? B.rneed[0] : B.rneed[1];
+    const bool rescan = B.dev->rescan != 0;
+    // the region census of this state: blocks with census > 0
+    for (int r = threadIdx.x; r < nreg; r += 1024) rc[r] = 0;
+    __syncthreads();
+    const int nlast = rescan ? nt : B.work[0];
+    for (int i = threadIdx.x; i < nlast; i += 1024) {
+        const int t = rescan ? i : B.work[2 + i];
+        if (cen[t] > 0) atomicAdd(rc + (t / c.tiles_x / SWE_REGION) * c.regions_x + (t % c.tiles_x) / SWE_REGION, 1);
+    }
+    __syncthreads();
+    // region flags of this state; the next state's region census starts at 0
+    for (int r = threadIdx.x; r < nreg; r += 1024) {
+        const int rx = r % c.regions_x, ry = r / c.regions_x;
+        const bool wet = rc[r] > 0 || (rx > 0 && rc[r - 1] > 0) || (rx < c.regions_x - 1 && rc[r + 1] > 0) ||
+                         (ry > 0 && rc[r - c.regions_x] > 0) || (ry < c.regions_y - 1 && rc[r + c.regions_x] > 0);
+        rn[r] = wet ? 1 : 0;
+    }
+    __syncthreads();
+    // regions examined, in chunks of 1024: their blocks, in chunks of 1024
+    for (int r0 = 0; r0 < nreg; r0 += 1024) {
+        const int r = r0 + (int)threadIdx.x;
+        const bool scan = r < nreg && (rescan || rn[r] || rn_prev[r]);
+        unsigned m = __ballot_sync(0xffffffffu, scan);
         if (lane == 0) wsum[w] = __popc(m);
         __syncthreads();
-        if (threadIdx.x == 0) {   // exclusive prefix over the warps, and the chunk's total
+        if (threadIdx.x == 0) {
             int acc = 0;
             for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
-            chunk = acc;
+            nscan = acc;
         }
         __syncthreads();
-        if (need) B.work[2 + base + wsum[w] + __popc(m & ((1u << lane) - 1u))] = tile;
+        if (scan) rlist[wsum[w] + __popc(m & ((1u << lane) - 1u))] = r;
         __syncthreads();
-        if (threadIdx.x == 0) base += chunk;
-        __syncthreads();
+        const int ns = nscan;
+        for (int j0 = 0; j0 < ns * SWE_REGION * SWE_REGION; j0 += 1024) {
+            const int j = j0 + (int)threadIdx.x;
+            bool need = false;
+            int tile = 0;
+            if (j < ns * SWE_REGION * SWE_REGION) {
+                const int reg = rlist[j / (SWE_REGION * SWE_REGION)], q = j % (SWE_REGION * SWE_REGION);
+                const int bx = (reg % c.regions_x) * SWE_REGION + q % SWE_REGION;
+                const int by = (reg / c.regions_x) * SWE_REGION + q / SWE_REGION;
+                if (bx < c.tiles_x && by < c.tiles_y) {
+                    tile = by * c.tiles_x + bx;
+                    const int l = bx > 0 ? bx - 1 : bx, rr = bx < c.tiles_x - 1 ? bx + 1 : bx;
+                    const int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
+                    const bool active = cen[tile] > 0 || cen[by * c.tiles_x + l] > 0 || cen[by * c.tiles_x + rr] > 0 ||
+                                        cen[d * c.tiles_x + bx] > 0 || cen[u * c.tiles_x + bx] > 0;
+                    need = active || !B.skipped[tile];
+                    if (!need) cen_next[tile] = 0;
+                }
+            }
+            m = __ballot_sync(0xffffffffu, need);
+            __syncthreads();   // rlist of this chunk stays read-only; wsum is reused below
+            if (lane == 0) wsum[w] = __popc(m);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
+                chunk = acc;
+            }
+            __syncthreads();
+            if (need) B.work[2 + base + wsum[w] + __popc(m & ((1u << lane) - 1u))] = tile;
+            __syncthreads();
+            if (threadIdx.x == 0) base += chunk;
+            __syncthreads();
+        }
     }
-    if (threadIdx.x == 0) B.work[0] = base;
+    if (threadIdx.x == 0) {
+        B.work[0] = base;
+        if (rescan) B.dev->rescan = 0;
+    }
 }
 
-// One step: one CUDA block per grid block; CUDA block i runs entry i of the
-// work list (a column band x row strip), blocks past the list's end return at
-// once.  With every block listed this is one block per grid block in order.
+// One step: CUDA block i runs entries i, i + gridDim.x, ... of the work list
+// (a column band x row strip each).  Launched with one CUDA block per grid
+// block (dense steps) each runs at most one entry and the blocks past the
+// list's end return at once; a smaller grid (sparse steps) walks the list.
 // FP32: three blocks per SM (80 registers, 73 KB of shared memory each); two
 // for the variants with source terms or the general laws, whose sweep does
 // not fit 80 registers without spills.
-template <typename T, int BW, bool SRC, bool GEN>
+template <typename T, int BW, bool SRC, bool GEN, bool WALK>
 __global__ void __launch_bounds__(BW, sizeof(T) == 4 ? ((SRC || GEN) ? 2 : 3) : 1) step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
-    const int i = blockIdx.x;
-    if (i >= B.work[0]) return;
-    const int tile = B.work[2 + i];
-    if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
-    step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+    const int count = B.work[0];
+    if (!WALK) {   // dense: at most one entry per CUDA block
+        const int i = blockIdx.x;
+        if (i >= count) return;
+        const int tile = B.work[2 + i];
+        if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
+        step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+        return;
+    }
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int tile = B.work[2 + i];
+        if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
+        step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+    }
 }
 
 // ----------------------------------------------- census + Eq. 7 terms of a state
@@ -868,7 +1004,10 @@ __global__ void __launch_bounds__(BW) init_kernel(SweConst c, SweBufs B) {
             cell_epilogue<T>(c, k, H, Hu, Hv, bb, tab<T>(B.ajn, mi), src, cnt, m0, m1, m2, st);
         }
     block_finish<T, BW>(cnt, m0, m1, m2, st, tile, (n & 1) ? B.census[1] : B.census[0], dev, 0);
-    if (threadIdx.x == 0) B.skipped[tile] = 0;
+    if (threadIdx.x == 0) {
+        B.skipped[tile] = 0;
+        if (tile == 0) dev->rescan = 1;   // the first compaction rebuilds the region census
+    }
 }
 
 // ------------------------------------------------------ dt (K3) and bookkeeping

@@ -16,42 +16,50 @@ template <typename T> size_t step_smem_bytes(int bw) {
 // variant compiles only the terms in use: inflow, rain and infiltration
 // (SRC), the general transport laws (GEN).
 template <typename T, int BW, bool SRC, bool GEN>
-static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
     // the shared-memory opt-in is a per-device function attribute: one bit
     // per device (devices beyond 64 set it on every launch)
     static std::atomic<unsigned long long> configured{0};
     const size_t smem = sizeof(StepSmem<T, BW>);
-    auto kern = step_kernel<T, BW, SRC, GEN>;
+    const int nt = c.tiles_x * c.tiles_y;
+    const bool walk = grid > 0 && grid < nt;
+    auto kern = walk ? step_kernel<T, BW, SRC, GEN, true> : step_kernel<T, BW, SRC, GEN, false>;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
     if (!bit || !(configured.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(step_kernel<T, BW, SRC, GEN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel<T, BW, SRC, GEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit, std::memory_order_release);
     }
     compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
-    kern<<<c.tiles_x * c.tiles_y, BW, smem, s>>>(c, b);
+    kern<<<walk ? grid : nt, BW, smem, s>>>(c, b);
     return cudaGetLastError();
 }
 
 inline bool uses_sources(const SweConst &c) { return c.nsrc > 0 || c.has_rain || c.has_beta; }
 inline bool uses_general_laws(const SweConst &c) { return c.aj_mode == 1 || !c.m_is_2; }
 
-template <typename T, int BW> static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+template <typename T, int BW>
+static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
     if constexpr (sizeof(T) == 8) {
-        return launch_step_v<T, BW, true, true>(c, b, s);   // the FP64 build (parity): the general variant
+        return launch_step_v<T, BW, true, true>(c, b, s, grid);   // the FP64 build (parity): the general variant
     } else {
         const bool src = uses_sources(c), gen = uses_general_laws(c);
-        if (src) return gen ? launch_step_v<T, BW, true, true>(c, b, s) : launch_step_v<T, BW, true, false>(c, b, s);
-        return gen ? launch_step_v<T, BW, false, true>(c, b, s) : launch_step_v<T, BW, false, false>(c, b, s);
+        if (src)
+            return gen ? launch_step_v<T, BW, true, true>(c, b, s, grid) : launch_step_v<T, BW, true, false>(c, b, s, grid);
+        return gen ? launch_step_v<T, BW, false, true>(c, b, s, grid) : launch_step_v<T, BW, false, false>(c, b, s, grid);
     }
 }
 
-template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s) {
-    if (bw == 128) return launch_step_bw<T, 128>(c, b, s);
-    return launch_step_bw<T, 256>(c, b, s);
+template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid) {
+    if (bw == 128) return launch_step_bw<T, 128>(c, b, s, grid);
+    return launch_step_bw<T, 256>(c, b, s, grid);
 }
 
 template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s) {
@@ -94,7 +102,7 @@ template <typename T> cudaError_t launch_bed_source(const SweConst &c, const Swe
 
 #define SWE_INSTANTIATE(T)                                                                                        \
     template size_t step_smem_bytes<T>(int);                                                                      \
-    template cudaError_t launch_step<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                   \
+    template cudaError_t launch_step<T>(const SweConst &, const SweBufs &, int, cudaStream_t, int);              \
     template cudaError_t launch_init<T>(const SweConst &, const SweBufs &, cudaStream_t);                        \
     template cudaError_t launch_between<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                \
     template cudaError_t launch_diag<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                   \

@@ -121,8 +121,10 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, v
     c.neg_tol = p.neg_tol >= 0 ? p.neg_tol : 1e-4;
     c.eps_f = float_floor(p.eps_wet);
     swe_fill_f32(c);
+    swe_set_regions(c);
 
-    // carve the scratch: bookkeeping | census x2 | skip flags | work list | source rows | Manning tables
+    // carve the scratch: bookkeeping | census x2 | skip flags | work list | source rows |
+    // region census | region flags x2 | Manning tables
     const size_t ntiles = (size_t)c.tiles_x * c.tiles_y;
     const size_t off_dev = 0;
     const size_t off_cen0 = align256(off_dev + sizeof(SweDev));
@@ -130,7 +132,11 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, v
     const size_t off_skip = align256(off_cen1 + ntiles * sizeof(int));
     const size_t off_work = align256(off_skip + ntiles);
     const size_t off_rows = align256(off_work + (ntiles + 2) * sizeof(int));
-    const size_t off_gn2 = align256(off_rows + ((size_t)p.ny + 1) * sizeof(int));
+    const size_t nreg = (size_t)c.regions_x * c.regions_y;
+    const size_t off_rc0 = align256(off_rows + ((size_t)p.ny + 1) * sizeof(int));
+    const size_t off_rn0 = align256(off_rc0 + nreg * sizeof(int));
+    const size_t off_rn1 = align256(off_rn0 + nreg);
+    const size_t off_gn2 = align256(off_rn1 + nreg);
     const size_t off_ajn = off_gn2 + 128;
     const size_t total = off_ajn + 128;
     if (total > SWE_NOALLOC_SCRATCH_BYTES) return err(SWE_EINVAL, "grid too large for the fixed 1 MiB scratch");
@@ -147,6 +153,9 @@ extern "C" swe_status swe_step_noalloc(const swe_params *pp, double manning_n, v
     b.skipped = base + off_skip;
     b.work = (int *)(base + off_work);
     b.src_rowptr = (const int *)(base + off_rows);
+    b.rcen = (int *)(base + off_rc0);
+    b.rneed[0] = base + off_rn0;
+    b.rneed[1] = base + off_rn1;
     b.src_x = nullptr;
     b.hyd_t = nullptr; b.hyd_q = nullptr; b.qb = nullptr;
     b.gn2 = base + off_gn2;

@@ -215,3 +215,20 @@ def ensemble_scenario(side: int, seed: int, manning: float, peak: float, d50_sca
     out.d50 = 5e-4 * d50_scale
     return out
 
+
+
+def sparse_lake(nx: int, ny: int, dx: float = 5.0, seed: int = 11, center=(128, 960), radius: int = 40,
+                rise: float = 1.5) -> Scenario:
+    """Mostly dry fractal terrain with one lake released from a circular
+    reservoir: water level `rise` metres above the terrain's highest point
+    inside a disc of `radius` cells at `center` (row, column), dry elsewhere,
+    at rest; uniform Manning n 0.03.  The lake's edge spreads across the
+    HGS blocks and regions around it while most of the domain stays dry."""
+    b = fractal_dem(nx, ny, seed)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    disc = (yy - center[0]) ** 2 + (xx - center[1]) ** 2 <= radius ** 2
+    eta = b[disc].max() + rise
+    H = np.where(disc, eta - b, 0.0)
+    Z = np.zeros_like(H)
+    return Scenario(nx, ny, dx, H, Z, Z.copy(), b, np.full((ny, nx), 0.03), manning_block=0,
+                    name=f"sparse_lake_{nx}x{ny}")

@@ -1,10 +1,12 @@
-"""Batched ensembles (one persistent launch advancing many scenarios): each
-scenario must evolve bit for bit as it does alone, the autotuner must keep
-that true, and the launch's bounded grid barrier must give up cleanly."""
+"""Batched ensembles (one persistent launch advancing many scenarios, work
+scheduled by dataflow): each scenario must evolve bit for bit as it does
+alone, the autotuner must keep that true, the members must match the oracle
+step by step, and the launch's bounded waits must give up cleanly."""
 import numpy as np
 import pytest
 
 from paper_2103_15196_gb300 import inputs as I
+from fp32_band import band_error, band_params
 
 pytestmark = pytest.mark.gpu
 
@@ -88,17 +90,18 @@ def test_ensemble_autotune_keeps_results(swe):
     E.close()
 
 
-def test_ensemble_barrier_gives_up_with_a_status(swe):
-    """The barrier is made to wait for one block that does not exist: every
-    block stops after the time limit, the host reads SWE_ETIMEOUT, and the
-    ensemble works again once the limit is back to normal."""
+def test_ensemble_wait_gives_up_with_a_status(swe):
+    """Every scenario step is made to wait for one work item that does not
+    exist: every block stops after the time limit, the host reads
+    SWE_ETIMEOUT, and the ensemble works again once the limit is back to
+    normal."""
     scs = _scenarios()[:3]
     E = swe.Ensemble([_spec(s) for s in scs], block_cols=256, tile_rows=32)
     for m, sc in zip(E.members, scs):
         _load(m, sc)
     E.set_timeout(0.2, extra_arrivals=1)
     with pytest.raises(swe.SweError) as e:
-        E.run(1)
+        E.run(3)   # the second step's items wait for the first step, which never completes
     assert e.value.status == swe.SWE_ETIMEOUT
     E.set_timeout(2.0, 0)
     for m, sc in zip(E.members, scs):
@@ -115,7 +118,8 @@ def test_ensemble_members_match_the_oracle_per_step(swe, orc):
     """Each member of one persistent ensemble launch against the FP64 oracle,
     one step at a time from the member's own FP32 state, element by element,
     within the per-step FP32 bound of the single-grid parity tests (4e-5 m on
-    H and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta); dt (Eq. 7) per member.
+    H and b, 4e-5 m^2/s + 2e-5 |Hu| on momenta; the oracle at the Shamov
+    threshold or at the edges of its FP32 decision band); dt (Eq. 7) per member.
     Members of uneven size: a ragged 333 x 271 grid with inflow (2 x 9 blocks
     of 248 x 32, ragged right and bottom), a 200 x 200 grid without sources,
     a tall 96 x 312 grid with inflow, a 64 x 64 grid; every one drifts so the
@@ -150,15 +154,17 @@ def test_ensemble_members_match_the_oracle_per_step(swe, orc):
             st, t = before[k]
             p = orc.Params(nx=m["nx"], ny=m["ny"], dx=m["dx"], d50=m["d50"], A_J=0.01)
             hydro = orc.Hydrograph(m["ht"], m["hq"]) if m["src"] is not None else None
-            o, info = orc.step(p, st, np.full((m["ny"], m["nx"]), m["n"]), src=m["src"], hydro=hydro, t=t)
+            ncell = np.full((m["ny"], m["nx"]), m["n"])
+            o, info = orc.step(p, st, ncell, src=m["src"], hydro=hydro, t=t)
+            outs = [o.arrays()] + [orc.step(pp, st, ncell, src=m["src"], hydro=hydro, t=t)[0].arrays()
+                                   for pp in band_params(p)[1:]]
             assert h.t - t == pytest.approx(info.dt, rel=1e-5), (it, k)
             got = h.get_state(np.float32)
             moved[k] = max(moved[k], np.abs(o.b - st.b).max())
             for q in range(4):
-                e = np.abs(got[q].astype(np.float64) - o.arrays()[q])
-                tol = 4e-5 + (2e-5 * np.abs(o.arrays()[q]) if q in (1, 2) else 0.0)
+                excess, e = band_error(got[q], outs, q)
                 worst[k, q] = max(worst[k, q], e.max())
-                assert np.all(e <= tol), (it, k, q, e.max())
+                assert np.all(excess <= 0), (it, k, q, e.max())
     E.close()
     assert np.all(moved > 1e-7), moved   # the bed moves in every member
     print("ensemble vs oracle, worst abs err per member (H, Hu, Hv, b):", worst.tolist())
