@@ -485,15 +485,18 @@ def run_surrogate(args, torch, swe):
 
     def sample_run(seed, Xs, Ys, count, k0):
         """count windows of one scenario, a skipped window between samples:
-        its start bed, one coupled step (the network's input state), then
-        the rest of the K coupled steps (the target)."""
+        its start bed, two coupled steps (the bed saved between them; the
+        network's input state), then the rest of the K coupled steps (the
+        target)."""
         sv = solver(scenario(seed))
         sv.run_steps(args.sur_spin)
         for j in range(count):
             net.save_bed(sv)
             sv.run_steps(1)
+            net.save_mid(sv)
+            sv.run_steps(1)
             net.pack_state(sv, Xs[4 * (k0 + j):4 * (k0 + j) + 4])
-            sv.run_steps(K - 1)
+            sv.run_steps(K - 2)
             net.pack_target(sv, Ys[4 * (k0 + j):4 * (k0 + j) + 4])
             sv.run_steps(K * args.sur_gap)
         sv.close()
@@ -510,28 +513,33 @@ def run_surrogate(args, torch, swe):
     ov = torch.empty((4, T, T), dtype=torch.float32, device="cuda")
 
     def validate():
-        """Relative L1 of the network and of the linear extrapolation alone
-        on held-out windows (output units)."""
-        e_net = e_lin = ref = 0.0
+        """Relative L1 on held-out windows (output units) of the network, of
+        the linear extrapolation of the two coupled steps (channel 6, the
+        network's base) and of the first step alone (channel 6 - channel 5),
+        both masked as the network's output is."""
+        e_net = e_lin = e_lin1 = ref = outside = 0.0
         for j in range(nval):
             net.forward(Xv[4 * j:4 * j + 4], ov, 4)
             torch.cuda.synchronize()
             o = ov.cpu().numpy().astype(np.float64)
             y = Yv[4 * j:4 * j + 4].cpu().numpy().astype(np.float64)
-            xs = Xv[4 * j:4 * j + 4, :, :, 6:8].float().cpu().numpy().astype(np.float64)
+            xs = Xv[4 * j:4 * j + 4, :, :, 5:8].float().cpu().numpy().astype(np.float64)
             e_net += np.abs(o - y).sum()
-            e_lin += np.abs(xs[..., 0] * xs[..., 1] - y).sum()
+            e_lin += np.abs(xs[..., 1] * xs[..., 2] - y).sum()
+            e_lin1 += np.abs((xs[..., 1] - xs[..., 0]) * xs[..., 2] - y).sum()
+            outside += np.abs(y * (xs[..., 2] == 0)).sum()
             ref += np.abs(y).sum()
-        return e_net / ref, e_lin / ref
+        validate.outside = outside / ref
+        return e_net / ref, e_lin / ref, e_lin1 / ref
 
     t_data = time.perf_counter() - t_all
     # training
     t0 = time.perf_counter()
     g = torch.Generator().manual_seed(0)
-    steps, first, last = 0, None, None
+    steps, losses = 0, []
     lr0 = args.sur_lr
     val_curve = []
-    v_net, v_lin = validate()
+    v_net, v_lin, v_lin1 = validate()
     best = (v_net, [net.params(i) for i in range(6)])
     val_curve.append((0, v_net))
     next_val = args.sur_train_seconds / args.sur_val_points
@@ -540,18 +548,17 @@ def run_surrogate(args, torch, swe):
             el = time.perf_counter() - t0
             frac = min(1.0, el / args.sur_train_seconds)
             loss = net.train_step(X[4 * i:4 * i + 4], Y[4 * i:4 * i + 4], 4, lr0 * (0.1 + 0.9 * (1 - frac)))
-            first = loss if first is None else first
-            last = loss
+            losses.append(loss)
             steps += 1
             if el >= next_val:
                 next_val += args.sur_train_seconds / args.sur_val_points
-                vn, _ = validate()
+                vn, _, _ = validate()
                 val_curve.append((steps, vn))
                 if vn < best[0]:
                     best = (vn, [net.params(j) for j in range(6)])
             if time.perf_counter() - t0 >= args.sur_train_seconds:
                 break
-    vn, _ = validate()
+    vn, _, _ = validate()
     val_curve.append((steps, vn))
     if vn < best[0]:
         best = (vn, [net.params(j) for j in range(6)])
@@ -611,9 +618,13 @@ def run_surrogate(args, torch, swe):
            "speedup": rate_s / rate_p, "rate_plain_s_per_s": rate_p, "rate_surrogate_s_per_s": rate_s,
            "K": K, "f": f, "judge_every": J, "loss": args.sur_loss, "lr": args.sur_lr, "bound": args.sur_bound, "windows": R,
            "stats": st.as_dict(), "variants": variants,
-           "validation": {"samples": nval * 4, "err_linear": v_lin, "err_network_best": best[0],
-                          "curve": val_curve},
-           "train_steps": steps, "train_loss_first": first, "train_loss_last": last,
+           "validation": {"samples": nval * 4, "err_linear": v_lin, "err_linear_first_step": v_lin1,
+                          "err_network_best": best[0], "gain_vs_linear": best[0] / v_lin,
+                          "change_outside_mask": validate.outside, "curve": val_curve},
+           "train_steps": steps,
+           # mean training loss over the first and the last twentieth of the steps
+           "train_loss_first": float(np.mean(losses[:max(1, len(losses) // 20)])),
+           "train_loss_last": float(np.mean(losses[-max(1, len(losses) // 20):])),
            "samples": nsnap * 4, "tile": T, "forward_ms_2048sq": fwd_ms,
            "plain_window_ms": wall_p * 1e3 / R,
            "seconds": {"data": t_data, "train": t_train, "eval": wall_p + wall_s},
@@ -765,7 +776,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-hgs-flood", action="store_true")
     ap.add_argument("--hgs-steps", type=int, default=200)
-    ap.add_argument("--hgs-tile-rows", type=int, default=32, help="block strip height of the dry-start flood leg")
+    ap.add_argument("--hgs-tile-rows", type=int, default=16, help="block strip height of the dry-start flood leg")
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-surrogate", action="store_true")
@@ -773,17 +784,18 @@ def main():
     ap.add_argument("--sur-samples", type=int, default=2000)
     ap.add_argument("--sur-snaps-per-run", type=int, default=25)
     ap.add_argument("--sur-spin", type=int, default=300)
-    ap.add_argument("--sur-train-seconds", type=float, default=30.0)
+    ap.add_argument("--sur-train-seconds", type=float, default=90.0)
     ap.add_argument("--sur-lr", type=float, default=1e-3)
-    ap.add_argument("--sur-windows", type=int, default=40)
+    ap.add_argument("--sur-windows", type=int, default=200)
     ap.add_argument("--sur-f", type=int, default=25)
     ap.add_argument("--sur-judge", type=int, default=20)
-    ap.add_argument("--sur-bound", type=float, default=0.5)
+    ap.add_argument("--sur-bound", type=float, default=0.3,
+                    help="judged relative L1 of the window's bed change above which the plain solver takes over")
     ap.add_argument("--sur-loss", default="l1", choices=["mse", "l1"])
     ap.add_argument("--sur-gap", type=int, default=1, help="windows skipped between training samples")
     ap.add_argument("--sur-val", type=int, default=80, help="held-out validation samples (tiles)")
     ap.add_argument("--sur-val-points", type=int, default=6)
-    ap.add_argument("--sur-variants", default="10:10,10:20,50:20",
+    ap.add_argument("--sur-variants", default="10:10,10:20,25:10",
                     help="extra f:judge_every evaluations of the trained network")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -280,22 +280,25 @@ swe_status swe_set_sediment(swe_handle *h, int on);
  * Learned bed surrogate (a project addition, not in the paper): a 6-layer
  * 3x3 convolutional network, 32 channels, BF16 weights and activations with
  * FP32 accumulation on the tensor cores (tcgen05), that predicts the bed
- * change over a window of K coupled steps (Eq. 1-6) from the state one
- * coupled step into the window.  Inputs are the solver state cut into T x T
+ * change over a window of K coupled steps (Eq. 1-6) from the state two
+ * coupled steps into the window.  Inputs are the solver state cut into T x T
  * tiles (batch index ty * ceil(nx/T) + tx) with 8 channels:
  *   0  (H - norm[0]) / norm[1]         1  (b - norm[2]) / norm[3]
  *   2  u / norm[4]                     3  v / norm[4]
- *   4, 5  the Shamov-gated Grass direction v|v|^2 (Eq. 3-5) / norm[5]
- *   6  p = (b - b_saved) / norm[7]: the first step's bed change, scaled so
- *      that p is the linear extrapolation of the window's change in output
- *      units (norm[7] = norm[6] / K)
+ *   4  the Shamov ratio |v| / v_k of Eq. 5 (at most 4; 0 on dry cells)
+ *   5  the second difference (b - b_mid) - (b_mid - b_saved) / (2 norm[7])
+ *   6  p = (b - b_saved) / (2 norm[7]): the change over the two steps,
+ *      scaled so that p is their linear extrapolation to the window in
+ *      output units (norm[7] = norm[6] / K); p minus channel 5 is the first
+ *      step's extrapolation alone
  *   7  m = 1 where a cell within 4 cells (Chebyshev distance) changed its
- *      bed in the first step, else 0 (the activity mask)
+ *      bed since b_saved, else 0 (the activity mask)
  * b_saved is the bed at the last swe_surrogate_save_bed call (the window's
- * start).  The network output is m (c + p), c the last convolution: a
- * learned correction of the linear extrapolation, zero where nothing moved.
- * Output unit: norm[6] metres of bed change.  Device tensors: X bf16
- * [B][T][T][8], targets/outputs float [B][T][T].  Training: MSE or L1
+ * start), b_mid the bed at the last swe_surrogate_save_mid call (after the
+ * window's first coupled step).  The network output is m (c + p), c the last
+ * convolution: a learned correction of the linear extrapolation, zero where
+ * nothing moved.  Output unit: norm[6] metres of bed change.  Device tensors:
+ * X bf16 [B][T][T][8], targets/outputs float [B][T][T].  Training: MSE or L1
  * loss, Adam (lr given, betas 0.9/0.999). */
 typedef struct swe_surrogate swe_surrogate;
 typedef struct {
@@ -305,7 +308,7 @@ typedef struct {
     double err_last, err_max, err_mean;  /* judged relative L1 error of the bed change */
     double err_zero_mean;     /* the same for predicting no change (1 by definition) */
     double err_persist_mean;  /* the same for repeating the last judged change */
-    double err_linear_mean;   /* the same for the linear extrapolation p alone */
+    double err_linear_mean;   /* the same for the two-step linear extrapolation p alone */
     double elev_err_max;      /* judged relative L1 error of the bed elevation itself */
     int mode;                 /* 0: surrogate windows, 1: plain (after a takeover) */
 } swe_surrogate_stats;
@@ -331,16 +334,19 @@ swe_status swe_surrogate_grads(swe_surrogate *s, int layer, float *host);
 /* Device pointer of an internal buffer: 0..4 layer outputs (bf16, 32 channels,
  * row-planar [B][T][4][T][8]), 5 the network output. */
 swe_status swe_surrogate_buffer(swe_surrogate *s, int index, void **ptr);
-/* save_bed remembers the FP32 handle's current bed (the window's start);
- * pack_state writes the handle's current state as input tiles (device X,
- * channels as above, relative to the saved bed); *batch gets the tile count;
+/* save_bed remembers the FP32 handle's current bed (the window's start),
+ * save_mid the bed after the window's first coupled step; pack_state writes
+ * the handle's current state (after the second) as input tiles (device X,
+ * channels as above, relative to the saved beds); *batch gets the tile count;
  * pack_target writes the bed change since save_bed in output units (device
  * float). */
 swe_status swe_surrogate_pack_state(swe_surrogate *s, swe_handle *h, void *X, int *batch);
 swe_status swe_surrogate_save_bed(swe_surrogate *s, swe_handle *h);
+swe_status swe_surrogate_save_mid(swe_surrogate *s, swe_handle *h);
 swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *target);
-/* Predicts the window's bed change from the handle's current state and sets
- * the bed to the saved bed plus that change.  The network runs only on the
+/* Predicts the window's bed change from the handle's current state (two
+ * coupled steps after save_bed, save_mid between them) and sets the bed to
+ * the saved bed plus that change.  The network runs only on the
  * halo tiles (116 x 116 interior cells plus a 6-cell margin, as 128 x 128
  * images) that hold a cell of the activity mask; elsewhere the prediction is
  * exactly 0.  Device work of a few kernels and one host sync for the tile
@@ -348,12 +354,13 @@ swe_status swe_surrogate_pack_target(swe_surrogate *s, swe_handle *h, float *tar
  * larger than max_batch tiles), SWE_ENOMEM (first call's scratch), SWE_ECUDA,
  * SWE_ETIMEOUT (a convolution's bounded wait gave up). */
 swe_status swe_surrogate_apply(swe_surrogate *s, swe_handle *h);
-/* Runs nwindows windows, each worth K coupled steps of bed evolution.  A
- * surrogate window saves the bed, runs one coupled step, predicts the
- * window's bed change (on the active halo tiles, as swe_surrogate_apply
- * does), advances the water K/f - 1 further steps and sets the
- * bed to the saved bed plus the prediction (replacing what those steps did to
- * it); its bed time is f times its water time.  Every judge_every-th window instead runs K coupled
+/* Runs nwindows windows, each worth K coupled steps of bed evolution (K/f
+ * must be at least 2).  A surrogate window saves the bed, runs two coupled
+ * steps (saving the bed between them), predicts the window's bed change (on
+ * the active halo tiles, as swe_surrogate_apply does), advances the water
+ * K/f - 2 further steps and sets the bed to the saved bed plus the prediction
+ * (replacing what those steps did to it); its bed time is f times its water
+ * time.  Every judge_every-th window instead runs K coupled
  * steps and judges the prediction against them; a judged bed-change error
  * above `bound` hands the rest to the plain solver.  *st accumulates (zero
  * it before the first call). */

@@ -613,7 +613,10 @@ __global__ void loss_grad(const float *__restrict__ out, const float *__restrict
 // Shamov ratio |v| / v_k of Eq. 5, the second difference of the bed over the
 // window's two coupled steps, their linear extrapolation p, and the activity
 // mask.  Dry cells: zero velocity and ratio.
-constexpr int kActR = 4;   // Chebyshev radius of the activity mask
+#ifndef SWE_ACT_R
+#define SWE_ACT_R 4
+#endif
+constexpr int kActR = SWE_ACT_R;   // Chebyshev radius of the activity mask
 
 __device__ __forceinline__ size_t tile_index(int x, int y, int T, int ntx) {
     return ((size_t)(y / T) * ntx + x / T) * T * T + (size_t)(y % T) * T + x % T;

@@ -62,6 +62,7 @@ struct swe_handle {
     int graph_steps = 0;
     int sparse_grid = 0;                // CUDA blocks of a sparse step (about one wave)
     int *h_hint = nullptr;              // pinned: blocks computed by the last step of the last replay
+    bool stepped = false;               // a step ran since the state was set (active_last is current)
     std::string err;
 };
 
@@ -411,6 +412,7 @@ extern "C" swe_status swe_set_rain(swe_handle *h, const double *sigma) {
 static swe_status read_dev(swe_handle *h) {
     CU(h, cudaMemcpyAsync(h->h_dev, h->b.dev, sizeof(SweDev), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
+    if (h->stepped && h->h_hint) *h->h_hint = h->h_dev->active_last;   // the launch hint, exact here
     return SWE_OK;
 }
 
@@ -458,6 +460,7 @@ extern "C" swe_status swe_set_state_ex(swe_handle *h, const void *H, const void 
     swe_status s = read_dev(h);
     if (s != SWE_OK) return s;
     h->state_set = true;
+    h->stepped = false;
     *h->h_hint = h->c.tiles_x * h->c.tiles_y;   // unknown activity: dense launches until a step tells
     h->tend_active = false;
     return check_status(h);
@@ -553,9 +556,9 @@ extern "C" swe_status swe_step(swe_handle *h, double *dt_taken) {
     swe_status s = free_stepping(h);
     if (s != SWE_OK) return s;
     CU(h, L_one_step(h, step_grid(h, *h->h_hint)));
+    h->stepped = true;
     s = read_dev(h);
     if (s != SWE_OK) return s;
-    *h->h_hint = h->h_dev->active_last;
     if (dt_taken) *dt_taken = h->h_dev->dt_last;
     return check_status(h);
 }
@@ -567,16 +570,22 @@ extern "C" swe_status swe_run_steps(swe_handle *h, int64_t nsteps) {
     swe_status s = free_stepping(h);
     if (s != SWE_OK) return s;
     // the hint is what the last replay left in pinned memory (possibly an older
-    // replay's if the last one is still running): it only picks the launch
-    const int grid = step_grid(h, *h->h_hint);
-    s = ensure_graph(h, grid > 0);
-    if (s != SWE_OK) return s;
+    // replay's if the last one is still running), or the last step's count
+    // read back: it only picks the launch, per replay
     int64_t left = nsteps;
-    while (left >= h->graph_steps) {
+    for (;;) {
+        const int grid = step_grid(h, *h->h_hint);
+        s = ensure_graph(h, grid > 0);
+        if (s != SWE_OK) return s;
+        if (left < h->graph_steps) {
+            for (; left > 0; --left) CU(h, L_one_step(h, grid));
+            break;
+        }
         CU(h, cudaGraphLaunch(h->graph, h->stream));
+        h->stepped = true;
         left -= h->graph_steps;
     }
-    for (; left > 0; --left) CU(h, L_one_step(h, grid));
+    if (nsteps > 0) h->stepped = true;
     return SWE_OK;
 }
 
@@ -596,10 +605,10 @@ extern "C" swe_status swe_advance(swe_handle *h, double t_end, int64_t *steps_ta
         if (s != SWE_OK) return s;
         if (h->h_dev->status) break;
         if (h->h_dev->done || !h->h_dev->scheduled) break;
-        if (h->h_dev->n != n0) *h->h_hint = h->h_dev->active_last;
         s = ensure_graph(h, step_grid(h, *h->h_hint) > 0);
         if (s != SWE_OK) return s;
         CU(h, cudaGraphLaunch(h->graph, h->stream));
+        h->stepped = true;
     }
     if (steps_taken) *steps_taken = h->h_dev->n - n0;
     return check_status(h);
@@ -719,6 +728,7 @@ int handle_state_changed(swe_handle *h) {
         cudaMemsetAsync(&h->b.dev->rescan, 1, 1, h->stream) != cudaSuccess)
         return SWE_ECUDA;
     *h->h_hint = (int)nt;
+    h->stepped = false;
     return SWE_OK;
 }
 
@@ -755,6 +765,7 @@ int handle_retile(swe_handle *h, int bw, int th) {
     c.tw = tw; c.th = th; c.tiles_x = tx; c.tiles_y = ty;
     swe_set_regions(c);
     *h->h_hint = (int)nt;
+    h->stepped = false;
     drop_graphs(h);
     if (!h->state_set) return SWE_OK;
     // census of the current state (its buffer is buf[n & 1]); the maxima the

@@ -52,11 +52,12 @@ __device__ inline unsigned long long global_ns() {
 // steps[k] = ENS_SYNC + 2k + 1 (steps completed in this launch).
 #define ENS_SYNC 4
 
-// GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; the
-// sources are always compiled in (scenarios carry inflow).  extra: completions
+// GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; FLD:
+// the rain and infiltration fields; the inflow is always compiled in
+// (scenarios carry inflow); two blocks per SM.  extra: completions
 // each scenario step waits for beyond its items (0; > 0 only to make the waits
 // run out in a test).
-template <int BW, bool GEN>
+template <int BW, bool GEN, bool FLD>
 __global__ void __launch_bounds__(BW, 2)
 ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items, int nitems, int nsteps,
                 unsigned *sync, unsigned extra, unsigned long long timeout_ns) {
@@ -96,7 +97,7 @@ ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items
         __syncthreads();
         if (s_stop) return;
         const EnsScen &sc = scen[w.x];
-        step_tile<float, BW, true, true, GEN>(sc.c, sc.B, w.y, w.z, S);
+        step_tile<float, BW, true, SWE_SRC_INFLOW | (FLD ? SWE_SRC_FIELDS : 0), GEN>(sc.c, sc.B, w.y, w.z, S);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();   // this item's state, census and maxima before its count
@@ -130,18 +131,19 @@ struct swe_ensemble {
     int nitems = 0;
     int grid = 0;            // co-resident blocks of the persistent kernel for bw
     bool gen = false;        // some scenario uses the general transport laws
+    bool fld = false;        // some scenario has a rain or infiltration field
     bool graph_ok = true;    // false if this driver cannot capture the persistent launch
 };
 
 namespace {
 
-template <int BW, bool GEN> int resident_blocks() {
+template <int BW, bool GEN, bool FLD> int resident_blocks() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = sizeof(StepSmem<float, BW>);
-    cudaFuncSetAttribute(ensemble_kernel<BW, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_kernel<BW, GEN>, BW, smem);
+    cudaFuncSetAttribute(ensemble_kernel<BW, GEN, FLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_kernel<BW, GEN, FLD>, BW, smem);
     return std::max(1, per) * sms;
 }
 
@@ -156,6 +158,7 @@ swe_status upload(swe_ensemble *e) {
     const int n = (int)e->members.size();
     std::vector<EnsScen> sc(n);
     std::vector<int4> items;
+    bool fld = false;
     for (int k = 0; k < n; ++k) {
         SweConst *c = nullptr;
         SweBufs *b = nullptr;
@@ -165,6 +168,7 @@ swe_status upload(swe_ensemble *e) {
         if (handle_free_stepping(e->members[k]) != SWE_OK) return SWE_ECUDA;
         sc[k].c = *c;
         sc[k].B = *b;
+        fld = fld || c->has_rain || c->has_beta;
         for (int by = 0; by < c->tiles_y; ++by)
             for (int bx = 0; bx < c->tiles_x; ++bx) items.push_back(make_int4(k, bx, by, 0));
     }
@@ -175,7 +179,8 @@ swe_status upload(swe_ensemble *e) {
         e->items_cap = items.size();
         clear_graphs(e);   // captured launches point at the old list
     }
-    if ((int)items.size() != e->nitems) clear_graphs(e);
+    if ((int)items.size() != e->nitems || fld != e->fld) clear_graphs(e);   // (also resets the grid)
+    e->fld = fld;
     e->nitems = (int)items.size();
     if (cudaMemcpyAsync(e->d_scen, sc.data(), n * sizeof(EnsScen), cudaMemcpyHostToDevice, e->stream) != cudaSuccess ||
         cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, e->stream) !=
@@ -184,7 +189,7 @@ swe_status upload(swe_ensemble *e) {
     return SWE_OK;
 }
 
-template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
+template <int BW, bool GEN, bool FLD> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
     const int grid = e->grid;
     const size_t smem = sizeof(StepSmem<float, BW>);
     const size_t words = ENS_SYNC + 2 * e->members.size();
@@ -198,13 +203,36 @@ template <int BW, bool GEN> cudaError_t launch_persistent(swe_ensemble *e, int n
     cfg.numAttrs = 0;   // no grid barrier: blocks need not be co-resident
     const EnsScen *sc = e->d_scen;
     const int4 *it = e->d_items;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN>, sc, it, e->nitems, nsteps, e->d_sync,
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN, FLD>, sc, it, e->nitems, nsteps, e->d_sync,
                               (unsigned)e->extra, e->timeout_ns);
 }
 
+int resident_for(const swe_ensemble *e) {
+    const int v = (e->bw == 128 ? 4 : 0) | (e->gen ? 2 : 0) | (e->fld ? 1 : 0);
+    switch (v) {
+    case 0: return resident_blocks<256, false, false>();
+    case 1: return resident_blocks<256, false, true>();
+    case 2: return resident_blocks<256, true, false>();
+    case 3: return resident_blocks<256, true, true>();
+    case 4: return resident_blocks<128, false, false>();
+    case 5: return resident_blocks<128, false, true>();
+    case 6: return resident_blocks<128, true, false>();
+    default: return resident_blocks<128, true, true>();
+    }
+}
+
 cudaError_t launch_any(swe_ensemble *e, int nsteps) {
-    if (e->gen) return e->bw == 128 ? launch_persistent<128, true>(e, nsteps) : launch_persistent<256, true>(e, nsteps);
-    return e->bw == 128 ? launch_persistent<128, false>(e, nsteps) : launch_persistent<256, false>(e, nsteps);
+    const int v = (e->bw == 128 ? 4 : 0) | (e->gen ? 2 : 0) | (e->fld ? 1 : 0);
+    switch (v) {
+    case 0: return launch_persistent<256, false, false>(e, nsteps);
+    case 1: return launch_persistent<256, false, true>(e, nsteps);
+    case 2: return launch_persistent<256, true, false>(e, nsteps);
+    case 3: return launch_persistent<256, true, true>(e, nsteps);
+    case 4: return launch_persistent<128, false, false>(e, nsteps);
+    case 5: return launch_persistent<128, false, true>(e, nsteps);
+    case 6: return launch_persistent<128, true, false>(e, nsteps);
+    default: return launch_persistent<128, true, true>(e, nsteps);
+    }
 }
 
 // The graph of one persistent launch of `nsteps` steps (cached per count).
@@ -311,8 +339,7 @@ extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
     swe_status s = upload(e);
     if (s != SWE_OK) return s;
     if (e->grid == 0)
-        e->grid = e->gen ? (e->bw == 128 ? resident_blocks<128, true>() : resident_blocks<256, true>())
-                         : (e->bw == 128 ? resident_blocks<128, false>() : resident_blocks<256, false>());
+        e->grid = resident_for(e);
     // one persistent launch per call (split only where steps x items would
     // overflow the 32-bit work counter)
     const int64_t max_chunk = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max(1, e->nitems));

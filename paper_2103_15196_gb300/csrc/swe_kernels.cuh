@@ -45,6 +45,9 @@ namespace swe_impl {
 // an index outside sets SWE_STATUS_BOUNDS in the device status word and the
 // access is skipped.  In the production build SWE_IN is the constant true.
 #define SWE_STATUS_BOUNDS 8u
+// source terms compiled into a step-kernel variant (template parameter SRC)
+#define SWE_SRC_INFLOW 1
+#define SWE_SRC_FIELDS 2
 #ifdef SWE_CHECKED
 __device__ inline bool swe_in(long long i, long long n, SweDev *dev) {
     if (i >= 0 && i < n) return true;
@@ -509,7 +512,7 @@ template <typename T> __device__ inline T tab(const void *p, int i) { return rei
 //   row s-3, and the y-face (s-4|s-3).
 // Every read of a neighbour column refers to a row finished at an earlier
 // position, so one __syncthreads per position suffices.
-template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
+template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
     static constexpr int RW = StepSmem<T, BW>::RW;
     StepSmem<T, BW> &S;
     const SweConst &c;
@@ -642,18 +645,20 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
             const V2<T> C = HB<P, 5>()[o];
             const T Hc = C.x, bc = C.y;
             bool src = false;
-            if (SRC && c.nsrc > 0 && SWE_IN(r + 1, c.ny + 1))
+            if ((SRC & SWE_SRC_INFLOW) && c.nsrc > 0 && SWE_IN(r + 1, c.ny + 1))
                 for (int q = B.src_rowptr[r]; q < B.src_rowptr[r + 1]; ++q)
                     if (SWE_IN(q, c.nsrc)) src |= (B.src_x[q] == x);
             const V4<T> f = S.xf[PM5_2][o], fw = S.xf[PM5_2][o - 1];
             const V2<T> w = q4<P, 5>(S.W)[o];
             T hn = Hc - k.dtdx * ((f.a - fw.a) + dG[0]);
-            if (src) hn = hn + k.dHs;
-            if (SRC && c.has_rain && SWE_IN((long long)r * c.nx + x, SWE_NCELL))
+            // the source increment is read only for the few source cells (not
+            // held in a register through the sweep)
+            if (src) hn = hn + T(COHERENT ? ((const volatile SweDev *)B.dev)->dHs : B.dev->dHs);
+            if ((SRC & SWE_SRC_FIELDS) && c.has_rain && SWE_IN((long long)r * c.nx + x, SWE_NCELL))
                 hn = hn + k.dt * tab<T>(B.rain, (long long)r * c.nx + x);
             T hun = Hc * w.x - k.dtdx * ((f.b - fw.b) + dG[1]);
             T hvn = Hc * w.y - k.dtdx * ((f.c - fw.c) + dG[2]);
-            if (SRC && c.has_beta && SWE_IN((long long)r * c.nx + x, SWE_NCELL)) {
+            if ((SRC & SWE_SRC_FIELDS) && c.has_beta && SWE_IN((long long)r * c.nx + x, SWE_NCELL)) {
                 // infiltration: at most the water present, with its share of momentum
                 T loss = k.dt * tab<T>(B.beta, (long long)r * c.nx + x);
                 if (loss > hn) loss = hn > T(0) ? hn : T(0);
@@ -738,10 +743,11 @@ template <typename T, int BW, bool COHERENT, bool SRC, bool GEN> struct Sweep {
 // One step of one block (column band bx, row strip by).  COHERENT selects
 // L2-coherent reads of the state, census and bookkeeping, needed when other
 // blocks of the same (persistent) launch rewrote them since its start.
-// SRC compiles in the inflow, rain and infiltration terms of the update, GEN
+// SRC compiles in the source terms of the update (SWE_SRC_INFLOW: the inflow
+// hydrograph; SWE_SRC_FIELDS: the rain and infiltration fields), GEN
 // the general transport laws (A_J from Eq. 4, m != 2); without them (not in
 // use) the kernel is markedly smaller, which its instruction fetch rewards.
-template <typename T, int BW, bool COHERENT, bool SRC, bool GEN>
+template <typename T, int BW, bool COHERENT, int SRC, bool GEN>
 __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, int bx, int by, StepSmem<T, BW> &S) {
     SweDev *dev = B.dev;
     const volatile SweDev *vdev = dev;
@@ -954,8 +960,9 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
 // FP32: three blocks per SM (80 registers, 73 KB of shared memory each); two
 // for the variants with source terms or the general laws, whose sweep does
 // not fit 80 registers without spills.
-template <typename T, int BW, bool SRC, bool GEN, bool WALK>
-__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? ((SRC || GEN) ? 2 : 3) : 1) step_kernel(SweConst c, SweBufs B) {
+template <typename T, int BW, int SRC, bool GEN, bool WALK>
+__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? ((SRC || GEN) ? 2 : 3) : 1)
+step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int count = B.work[0];

@@ -13,9 +13,11 @@ template <typename T> size_t step_smem_bytes(int bw) {
 
 // One step: the work list of the blocks to run (compact_kernel), then one
 // CUDA block per grid block, the unlisted ones returning at once.  The kernel
-// variant compiles only the terms in use: inflow, rain and infiltration
-// (SRC), the general transport laws (GEN).
-template <typename T, int BW, bool SRC, bool GEN>
+// variant compiles only the terms in use: the inflow, and the rain and
+// infiltration fields (SRC bits), the general transport laws (GEN).  The
+// variant with none of them runs three blocks per SM, the others two (at
+// three their sweep spills).
+template <typename T, int BW, int SRC, bool GEN>
 static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
     // the shared-memory opt-in is a per-device function attribute: one bit
     // per device (devices beyond 64 set it on every launch)
@@ -42,18 +44,28 @@ static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream
     return cudaGetLastError();
 }
 
-inline bool uses_sources(const SweConst &c) { return c.nsrc > 0 || c.has_rain || c.has_beta; }
+inline int source_terms(const SweConst &c) {
+    return (c.nsrc > 0 ? SWE_SRC_INFLOW : 0) | ((c.has_rain || c.has_beta) ? SWE_SRC_FIELDS : 0);
+}
 inline bool uses_general_laws(const SweConst &c) { return c.aj_mode == 1 || !c.m_is_2; }
+
+template <typename T, int BW, int SRC>
+static cudaError_t launch_step_s(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
+    return uses_general_laws(c) ? launch_step_v<T, BW, SRC, true>(c, b, s, grid) : launch_step_v<T, BW, SRC, false>(c, b, s, grid);
+}
 
 template <typename T, int BW>
 static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
     if constexpr (sizeof(T) == 8) {
-        return launch_step_v<T, BW, true, true>(c, b, s, grid);   // the FP64 build (parity): the general variant
+        // the FP64 build (parity): the general variant
+        return launch_step_v<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS, true>(c, b, s, grid);
     } else {
-        const bool src = uses_sources(c), gen = uses_general_laws(c);
-        if (src)
-            return gen ? launch_step_v<T, BW, true, true>(c, b, s, grid) : launch_step_v<T, BW, true, false>(c, b, s, grid);
-        return gen ? launch_step_v<T, BW, false, true>(c, b, s, grid) : launch_step_v<T, BW, false, false>(c, b, s, grid);
+        switch (source_terms(c)) {
+        case 0: return launch_step_s<T, BW, 0>(c, b, s, grid);
+        case SWE_SRC_INFLOW: return launch_step_s<T, BW, SWE_SRC_INFLOW>(c, b, s, grid);
+        case SWE_SRC_FIELDS: return launch_step_s<T, BW, SWE_SRC_FIELDS>(c, b, s, grid);
+        default: return launch_step_s<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS>(c, b, s, grid);
+        }
     }
 }
 

@@ -155,6 +155,7 @@ def load_library(build_if_missing: bool = True, checked: bool = False):
         "swe_surrogate_buffer": [vp, ctypes.c_int, ctypes.POINTER(vp)],
         "swe_surrogate_pack_state": [vp, H, vp, ctypes.POINTER(ctypes.c_int)],
         "swe_surrogate_save_bed": [vp, H],
+        "swe_surrogate_save_mid": [vp, H],
         "swe_surrogate_pack_target": [vp, H, vp],
         "swe_surrogate_apply": [vp, H],
         "swe_surrogate_run": [vp, H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -504,6 +505,10 @@ class Surrogate:
 
     def save_bed(self, solver):
         self._check(self._L.swe_surrogate_save_bed(self._h, solver._h))
+
+    def save_mid(self, solver):
+        """The bed after the window's first coupled step (channels 5 and 6)."""
+        self._check(self._L.swe_surrogate_save_mid(self._h, solver._h))
 
     def pack_target(self, solver, target):
         self._check(self._L.swe_surrogate_pack_target(self._h, solver._h, self._p(target)))
