@@ -14,9 +14,8 @@ template <typename T> size_t step_smem_bytes(int bw) {
 // One step: the work list of the blocks to run (compact_kernel), then one
 // CUDA block per grid block, the unlisted ones returning at once.  The kernel
 // variant compiles only the terms in use: the inflow, and the rain and
-// infiltration fields (SRC bits), the general transport laws (GEN).  The
-// variant with none of them runs three blocks per SM, the others two (at
-// three their sweep spills).
+// infiltration fields (SRC bits), the general transport laws (GEN); every
+// FP32 variant runs three blocks per SM.
 template <typename T, int BW, int SRC, bool GEN>
 static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
     // the shared-memory opt-in is a per-device function attribute: one bit
