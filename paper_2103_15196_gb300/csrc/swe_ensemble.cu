@@ -96,19 +96,24 @@ ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items
         }
         __syncthreads();
         if (s_stop) return;
-        const EnsScen &sc = scen[w.x];
-        step_tile<float, BW, true, SWE_SRC_INFLOW | (FLD ? SWE_SRC_FIELDS : 0), GEN>(sc.c, sc.B, w.y, w.z, S);
+        step_tile<float, BW, true, SWE_SRC_INFLOW | (FLD ? SWE_SRC_FIELDS : 0), GEN>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
         __syncthreads();
         if (threadIdx.x == 0) {
+            // the item again from shared memory: nothing of it need stay in a
+            // register through the sweep
+            const long long g2 = s_g;
+            const int step2 = (int)(g2 / nitems);
+            const int4 w2 = items[g2 % nitems];
+            const EnsScen &sc = scen[w2.x];
             __threadfence();   // this item's state, census and maxima before its count
             const unsigned target = (unsigned)(sc.c.tiles_x * sc.c.tiles_y) + extra;
-            if (atomicAdd(sync + ENS_SYNC + 2 * w.x, 1u) + 1u == target) {
+            if (atomicAdd(sync + ENS_SYNC + 2 * w2.x, 1u) + 1u == target) {
                 // the scenario's step is complete: commit it, form its next dt
-                atomicExch(sync + ENS_SYNC + 2 * w.x, 0u);
+                atomicExch(sync + ENS_SYNC + 2 * w2.x, 0u);
                 __threadfence();
                 between_body<float>(sc.c, sc.B, 1);
                 __threadfence();
-                atomicExch(sync + ENS_SYNC + 2 * w.x + 1, (unsigned)(step + 1));
+                atomicExch(sync + ENS_SYNC + 2 * w2.x + 1, (unsigned)(step2 + 1));
             }
         }
     }
