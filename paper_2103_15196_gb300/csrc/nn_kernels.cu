@@ -845,6 +845,7 @@ __global__ void scatter_pred(int nx, int ny, int T, int ntx, const float *__rest
 // accumulation, FP32 master weights with Adam.
 // ======================================================================
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <random>
@@ -911,13 +912,18 @@ cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, con
     auto kern = conv3x3_ws<CIN, NOUT, EPI>;
     // enough shared memory that the CTAs of one SM fit its 512 TMEM columns
     static const size_t smem = std::max<size_t>(WC::smem(), (size_t)(227 * 1024) / (512 / WC::TCOLS) - 1024);
-    static int resident = 0;
+    // the function attributes and the resident CTA count, per device (the
+    // attributes are per-device settings; devices beyond 64 redo them)
+    static std::atomic<int> resident_of[64];
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    int resident = (dev >= 0 && dev < 64) ? resident_of[dev].load(std::memory_order_acquire) : 0;
     if (resident == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        int sms = 0, smem_sm = 0, reserved = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
@@ -925,6 +931,7 @@ cudaError_t conv(swe_surrogate *s, const __nv_bfloat16 *X, const NnLayer &l, con
         // CTAs per SM: shared memory, tensor memory (512 columns), threads
         const int per_sm = std::min({smem_sm / (int)(smem + reserved), 512 / WC::TCOLS, 2048 / 192});
         resident = std::max(1, per_sm) * sms;
+        if (dev >= 0 && dev < 64) resident_of[dev].store(resident, std::memory_order_release);
     }
     // one wave: the column bands x images share the resident CTAs, each CTA
     // streams a run of rows (a multiple of 4, at least 8, to amortise its set-up)
