@@ -95,9 +95,13 @@ static void dev_free(swe_handle *h, void *p) {
 
 // ---------------------------------------------------------------- launchers
 
-static cudaError_t L_step(swe_handle *h, int grid) {
-    return is_f32(h) ? launch_step<float>(h->c, h->b, h->bw, h->stream, grid)
-                     : launch_step<double>(h->c, h->b, h->bw, h->stream, grid);
+static cudaError_t L_step(swe_handle *h, int grid, bool list) {
+    return is_f32(h) ? launch_step<float>(h->c, h->b, h->bw, h->stream, grid, list)
+                     : launch_step<double>(h->c, h->b, h->bw, h->stream, grid, list);
+}
+static cudaError_t L_between_compact(swe_handle *h) {
+    return is_f32(h) ? launch_between_compact<float>(h->c, h->b, h->stream)
+                     : launch_between_compact<double>(h->c, h->b, h->stream);
 }
 static cudaError_t L_between(swe_handle *h, int commit) {
     return is_f32(h) ? launch_between<float>(h->c, h->b, commit, h->stream)
@@ -110,10 +114,13 @@ static cudaError_t L_bed(swe_handle *h) {
     return is_f32(h) ? launch_bed_source<float>(h->c, h->b, h->stream) : launch_bed_source<double>(h->c, h->b, h->stream);
 }
 // grid: 0 for a dense step, > 0 for a sparse one (see launch_step)
-static cudaError_t L_one_step(swe_handle *h, int grid = 0) {
-    cudaError_t e = L_step(h, grid);
+// One step: (the work list), the step, the bed source, then the commit and
+// the next step's work list in one launch.  list = false only for a step that
+// directly follows another one on the stream (inside a graph).
+static cudaError_t L_one_step(swe_handle *h, int grid = 0, bool list = true) {
+    cudaError_t e = L_step(h, grid, list);
     if (e == cudaSuccess && h->c.has_qb) e = L_bed(h);
-    if (e == cudaSuccess) e = L_between(h, 1);
+    if (e == cudaSuccess) e = L_between_compact(h);
     return e;
 }
 
@@ -535,7 +542,7 @@ static swe_status ensure_graph(swe_handle *h, bool sparse) {
     cudaGraph_t g;
     CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < m && e == cudaSuccess; ++i) e = L_one_step(h, sparse ? h->sparse_grid : 0);
+    for (int i = 0; i < m && e == cudaSuccess; ++i) e = L_one_step(h, sparse ? h->sparse_grid : 0, i == 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->h_hint, &h->b.dev->active_last, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);

@@ -91,10 +91,15 @@ struct SweBufs {
 namespace swe_impl {
 template <typename T> size_t step_smem_bytes(int bw);
 // grid: 0 launches one CUDA block per grid block; > 0 launches at most that
-// many blocks, each walking the work list (for sparse steps)
-template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid = 0);
+// many blocks, each walking the work list (for sparse steps).  list: form the
+// work list first (false only right after launch_between_compact on the
+// same stream, which formed it)
+template <typename T>
+cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid = 0, bool list = true);
 template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s);
 template <typename T> cudaError_t launch_between(const SweConst &c, const SweBufs &b, int commit, cudaStream_t s);
+// launch_between(commit = 1) followed by the next step's work list, in one launch
+template <typename T> cudaError_t launch_between_compact(const SweConst &c, const SweBufs &b, cudaStream_t s);
 template <typename T> cudaError_t launch_diag(const SweConst &c, const SweBufs &b, int nblocks, cudaStream_t s);
 template <typename T> cudaError_t launch_convert_in(const SweConst &c, void *dst, const void *H, const void *Hu,
                                                     const void *Hv, const void *bb, int src_is_f64, cudaStream_t s);

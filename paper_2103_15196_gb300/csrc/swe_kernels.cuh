@@ -853,13 +853,15 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
 // in work[0]; the census of the next state is written as 0 for every examined
 // block left out.  Without the dry-block skip every block is listed.  One
 // block of 1024 threads (T: the state type, for one instance per precision's
-// translation unit).
+// translation unit).  The step index and the rescan flag are read through a
+// volatile pointer: in between_compact_kernel thread 0 has just rewritten them.
 template <typename T>
-__global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
+__device__ __forceinline__ void compact_body(const SweConst &c, const SweBufs &B) {
     __shared__ int wsum[32];
     __shared__ int base, chunk, nscan;
     __shared__ int rlist[1024];
-    const long long n = B.dev->n;
+    const volatile SweDev *vd = B.dev;
+    const long long n = vd->n;
     const int par = (int)(n & 1);
     const int *cen = par ? B.census[1] : B.census[0];
     int *cen_next = par ? B.census[0] : B.census[1];
@@ -879,7 +881,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
     int *rc = B.rcen;
     unsigned char *rn = par ? B.rneed[1] : B.rneed[0];
     const unsigned char *rn_prev = par ? B.rneed[0] : B.rneed[1];
-    const bool rescan = B.dev->rescan != 0;
+    const bool rescan = vd->rescan != 0;
     // the region census of this state: blocks with census > 0
     for (int r = threadIdx.x; r < nreg; r += 1024) rc[r] = 0;
     __syncthreads();
@@ -952,6 +954,9 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) {
         if (rescan) B.dev->rescan = 0;
     }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) { compact_body<T>(c, B); }
 
 // One step: CUDA block i runs entries i, i + gridDim.x, ... of the work list
 // (a column band x row strip each).  Launched with one CUDA block per grid
@@ -1106,6 +1111,18 @@ __device__ void between_body(const SweConst &c, const SweBufs &B, int mode) {
 
 template <typename T>
 __global__ void between_kernel(SweConst c, SweBufs B, int mode) { between_body<T>(c, B, mode); }
+
+// The end of a step and the start of the next in one launch: thread 0 commits
+// the step and forms the next dt (between_body, mode 1), then the block lists
+// the blocks of the next step (compact_body) from the census just committed.
+// (Listing twice for one state gives the same list, so a step may still be
+// preceded by its own compaction.)
+template <typename T>
+__global__ void __launch_bounds__(1024) between_compact_kernel(SweConst c, SweBufs B) {
+    if (threadIdx.x == 0) between_body<T>(c, B, 1);
+    __syncthreads();
+    compact_body<T>(c, B);
+}
 
 // b += dt q / (1 - psi) on the freshly written buffer (Eq. 1 bed source).
 template <typename T>

@@ -11,13 +11,14 @@ template <typename T> size_t step_smem_bytes(int bw) {
     return bw == 128 ? sizeof(StepSmem<T, 128>) : sizeof(StepSmem<T, 256>);
 }
 
-// One step: the work list of the blocks to run (compact_kernel), then one
-// CUDA block per grid block, the unlisted ones returning at once.  The kernel
-// variant compiles only the terms in use: the inflow, and the rain and
-// infiltration fields (SRC bits), the general transport laws (GEN); every
-// FP32 variant runs three blocks per SM.
+// One step: the work list of the blocks to run (compact_kernel, left out
+// when the launch before it on the stream, between_compact_kernel, formed
+// it), then one CUDA block per grid block, the unlisted ones returning at
+// once.  The kernel variant compiles only the terms in use: the inflow, and
+// the rain and infiltration fields (SRC bits), the general transport laws
+// (GEN); every FP32 variant runs three blocks per SM.
 template <typename T, int BW, int SRC, bool GEN>
-static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
+static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid, bool list) {
     // the shared-memory opt-in is a per-device function attribute: one bit
     // per device (devices beyond 64 set it on every launch)
     static std::atomic<unsigned long long> configured{0};
@@ -38,7 +39,7 @@ static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit, std::memory_order_release);
     }
-    compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
+    if (list) compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
     kern<<<walk ? grid : nt, BW, smem, s>>>(c, b);
     return cudaGetLastError();
 }
@@ -49,28 +50,30 @@ inline int source_terms(const SweConst &c) {
 inline bool uses_general_laws(const SweConst &c) { return c.aj_mode == 1 || !c.m_is_2; }
 
 template <typename T, int BW, int SRC>
-static cudaError_t launch_step_s(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
-    return uses_general_laws(c) ? launch_step_v<T, BW, SRC, true>(c, b, s, grid) : launch_step_v<T, BW, SRC, false>(c, b, s, grid);
+static cudaError_t launch_step_s(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid, bool list) {
+    return uses_general_laws(c) ? launch_step_v<T, BW, SRC, true>(c, b, s, grid, list)
+                                : launch_step_v<T, BW, SRC, false>(c, b, s, grid, list);
 }
 
 template <typename T, int BW>
-static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid) {
+static cudaError_t launch_step_bw(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid, bool list) {
     if constexpr (sizeof(T) == 8) {
         // the FP64 build (parity): the general variant
-        return launch_step_v<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS, true>(c, b, s, grid);
+        return launch_step_v<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS, true>(c, b, s, grid, list);
     } else {
         switch (source_terms(c)) {
-        case 0: return launch_step_s<T, BW, 0>(c, b, s, grid);
-        case SWE_SRC_INFLOW: return launch_step_s<T, BW, SWE_SRC_INFLOW>(c, b, s, grid);
-        case SWE_SRC_FIELDS: return launch_step_s<T, BW, SWE_SRC_FIELDS>(c, b, s, grid);
-        default: return launch_step_s<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS>(c, b, s, grid);
+        case 0: return launch_step_s<T, BW, 0>(c, b, s, grid, list);
+        case SWE_SRC_INFLOW: return launch_step_s<T, BW, SWE_SRC_INFLOW>(c, b, s, grid, list);
+        case SWE_SRC_FIELDS: return launch_step_s<T, BW, SWE_SRC_FIELDS>(c, b, s, grid, list);
+        default: return launch_step_s<T, BW, SWE_SRC_INFLOW | SWE_SRC_FIELDS>(c, b, s, grid, list);
         }
     }
 }
 
-template <typename T> cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid) {
-    if (bw == 128) return launch_step_bw<T, 128>(c, b, s, grid);
-    return launch_step_bw<T, 256>(c, b, s, grid);
+template <typename T>
+cudaError_t launch_step(const SweConst &c, const SweBufs &b, int bw, cudaStream_t s, int grid, bool list) {
+    if (bw == 128) return launch_step_bw<T, 128>(c, b, s, grid, list);
+    return launch_step_bw<T, 256>(c, b, s, grid, list);
 }
 
 template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &b, cudaStream_t s) {
@@ -81,6 +84,11 @@ template <typename T> cudaError_t launch_init(const SweConst &c, const SweBufs &
 
 template <typename T> cudaError_t launch_between(const SweConst &c, const SweBufs &b, int commit, cudaStream_t s) {
     between_kernel<T><<<1, 1, 0, s>>>(c, b, commit);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_between_compact(const SweConst &c, const SweBufs &b, cudaStream_t s) {
+    between_compact_kernel<T><<<1, 1024, 0, s>>>(c, b);
     return cudaGetLastError();
 }
 
@@ -113,9 +121,10 @@ template <typename T> cudaError_t launch_bed_source(const SweConst &c, const Swe
 
 #define SWE_INSTANTIATE(T)                                                                                        \
     template size_t step_smem_bytes<T>(int);                                                                      \
-    template cudaError_t launch_step<T>(const SweConst &, const SweBufs &, int, cudaStream_t, int);              \
+    template cudaError_t launch_step<T>(const SweConst &, const SweBufs &, int, cudaStream_t, int, bool);        \
     template cudaError_t launch_init<T>(const SweConst &, const SweBufs &, cudaStream_t);                        \
     template cudaError_t launch_between<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                \
+    template cudaError_t launch_between_compact<T>(const SweConst &, const SweBufs &, cudaStream_t);             \
     template cudaError_t launch_diag<T>(const SweConst &, const SweBufs &, int, cudaStream_t);                   \
     template cudaError_t launch_convert_in<T>(const SweConst &, void *, const void *, const void *, const void *, \
                                               const void *, int, cudaStream_t);                                   \
