@@ -406,16 +406,17 @@ def run_hgs_flood(args, torch, swe):
     """The dry-block skip (K1, Sec. 3) on the kind of scene it is for: the
     flood-channel terrain at the benchmark's size, initially dry, water
     entering through the channel head (inflow hydrograph peaking at
-    500 m^3/s).  The same steps with the skip on and off; rates count every
-    cell of the grid per step."""
+    500 m^3/s).  The same steps with the skip on and off (off: on the same
+    blocks and on the library's default blocks for the grid, the speed-up
+    taken against the faster); rates count every cell of the grid per step."""
     from paper_2103_15196_gb300 import inputs as I
     n, K, W = args.size, args.hgs_steps, 5
     sc = I.flood_channel(n, dx=5.0, seed=2, peak=500.0)
     stream = torch.cuda.Stream()
     out = {}
-    for name, skip in (("on", 1), ("off", 0)):
+    for name, skip, rows in (("on", 1, args.hgs_tile_rows), ("off", 0, args.hgs_tile_rows), ("off_default_blocks", 0, 0)):
         S = swe.Solver(n, n, 5.0, precision="fp32", stream=stream.cuda_stream, hgs_skip=skip,
-                       tile_rows=args.hgs_tile_rows)
+                       tile_rows=rows)
         S.set_manning(sc.manning, block=sc.manning_block)
         S.set_sources(sc.src, sc.hydro_t, sc.hydro_Q)
         S.set_state(*(np.asarray(a, dtype=np.float32) for a in (sc.H, sc.Hu, sc.Hv, sc.b)))
@@ -433,10 +434,12 @@ def run_hgs_flood(args, torch, swe):
                      "active_cell_fraction": (d1["cells_computed"] - d0["cells_computed"]) / (float(n) * n * K),
                      "wet_cells_end": d1["wet_cells"], "t_end": d1["t"]}
         S.close()
+    off = max(out["off"]["value"], out["off_default_blocks"]["value"])
     return {"workload": f"flood channel {n}x{n}, initially dry, inflow on the channel head, steps {W}..{W + K}",
             "tile_rows": args.hgs_tile_rows,
             "unit": UNIT, "skip_on": out["on"], "skip_off": out["off"],
-            "speedup": out["on"]["value"] / out["off"]["value"]}
+            "skip_off_default_blocks": out["off_default_blocks"],
+            "speedup": out["on"]["value"] / off}
 
 
 def run_surrogate(args, torch, swe):
@@ -776,7 +779,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-hgs-flood", action="store_true")
     ap.add_argument("--hgs-steps", type=int, default=200)
-    ap.add_argument("--hgs-tile-rows", type=int, default=16, help="block strip height of the dry-start flood leg")
+    ap.add_argument("--hgs-tile-rows", type=int, default=8, help="block strip height of the dry-start flood leg")
     ap.add_argument("--ens-n", type=int, default=64)
     ap.add_argument("--ens-steps", type=int, default=100)
     ap.add_argument("--no-surrogate", action="store_true")

@@ -771,10 +771,13 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
         auto cen = [&](int i) {
             return SWE_IN(i, c.tiles_x * c.tiles_y) ? (COHERENT ? __ldcg(cen_in + i) : cen_in[i]) : 0;
         };
-        bool active = cen(tile) > 0 || cen(by * c.tiles_x + l) > 0 || cen(by * c.tiles_x + r) > 0 ||
-                      cen(d * c.tiles_x + bx) > 0 || cen(u * c.tiles_x + bx) > 0;
-        // the skip flag was written by whichever block ran this tile last
+        // every count and the skip flag loaded first (one wait for memory, not
+        // one per term of a short-circuit test); the skip flag was written by
+        // whichever block ran this tile last
+        const int k0 = cen(tile), k1 = cen(by * c.tiles_x + l), k2 = cen(by * c.tiles_x + r);
+        const int k3 = cen(d * c.tiles_x + bx), k4 = cen(u * c.tiles_x + bx);
         const bool was_skipped = COHERENT ? __ldcg(B.skipped + tile) != 0 : B.skipped[tile] != 0;
+        const bool active = (k0 > 0) | (k1 > 0) | (k2 > 0) | (k3 > 0) | (k4 > 0);
         if (!active) {
             if (!was_skipped) {
                 int x1 = min(tx0 + c.tw, c.nx);
@@ -838,6 +841,20 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     block_finish<T, BW>((int)(w.cnt & 0xffffffu), w.m0, w.m1, w.m2, w.cnt >> 24, tile, cen_out, dev, 1);
 }
 
+// The 32 per-warp counts in v[] replaced by their exclusive prefix sums and
+// the total written to *total, by one warp (lane = its lane index).
+__device__ __forceinline__ void warp_exclusive_scan32(int *v, int lane, int *total) {
+    const int own = v[lane];
+    int x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    v[lane] = x - own;
+    if (lane == 31) *total = x;
+}
+
 // The blocks the next step must run (HGS, Sec. 3: regions of SWE_REGION x
 // SWE_REGION blocks above the blocks, compacted): those active by the K1 rule
 // (the block or one of its four edge neighbours holds water or a source) and
@@ -891,26 +908,26 @@ __device__ __forceinline__ void compact_body(const SweConst &c, const SweBufs &B
         if (cen[t] > 0) atomicAdd(rc + (t / c.tiles_x / SWE_REGION) * c.regions_x + (t % c.tiles_x) / SWE_REGION, 1);
     }
     __syncthreads();
-    // region flags of this state; the next state's region census starts at 0
-    for (int r = threadIdx.x; r < nreg; r += 1024) {
-        const int rx = r % c.regions_x, ry = r / c.regions_x;
-        const bool wet = rc[r] > 0 || (rx > 0 && rc[r - 1] > 0) || (rx < c.regions_x - 1 && rc[r + 1] > 0) ||
-                         (ry > 0 && rc[r - c.regions_x] > 0) || (ry < c.regions_y - 1 && rc[r + c.regions_x] > 0);
-        rn[r] = wet ? 1 : 0;
-    }
-    __syncthreads();
-    // regions examined, in chunks of 1024: their blocks, in chunks of 1024
+    // regions examined, in chunks of 1024: their blocks, in chunks of 1024.
+    // A region's flag for this state (it or an edge neighbour holds water) is
+    // formed by the thread that examines it, from loads issued together
+    // (clamped neighbour indices, no short-circuit test).
     for (int r0 = 0; r0 < nreg; r0 += 1024) {
         const int r = r0 + (int)threadIdx.x;
-        const bool scan = r < nreg && (rescan || rn[r] || rn_prev[r]);
+        bool scan = false;
+        if (r < nreg) {
+            const int rx = r % c.regions_x, ry = r / c.regions_x;
+            const int q0 = rc[r], q1 = rc[rx > 0 ? r - 1 : r], q2 = rc[rx < c.regions_x - 1 ? r + 1 : r];
+            const int q3 = rc[ry > 0 ? r - c.regions_x : r], q4 = rc[ry < c.regions_y - 1 ? r + c.regions_x : r];
+            const bool prev = rn_prev[r] != 0;
+            const bool wet = (q0 > 0) | (q1 > 0) | (q2 > 0) | (q3 > 0) | (q4 > 0);
+            rn[r] = wet ? 1 : 0;
+            scan = rescan || wet || prev;
+        }
         unsigned m = __ballot_sync(0xffffffffu, scan);
         if (lane == 0) wsum[w] = __popc(m);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
-            nscan = acc;
-        }
+        if (w == 0) warp_exclusive_scan32(wsum, lane, &nscan);
         __syncthreads();
         if (scan) rlist[wsum[w] + __popc(m & ((1u << lane) - 1u))] = r;
         __syncthreads();
@@ -927,9 +944,11 @@ __device__ __forceinline__ void compact_body(const SweConst &c, const SweBufs &B
                     tile = by * c.tiles_x + bx;
                     const int l = bx > 0 ? bx - 1 : bx, rr = bx < c.tiles_x - 1 ? bx + 1 : bx;
                     const int d = by > 0 ? by - 1 : by, u = by < c.tiles_y - 1 ? by + 1 : by;
-                    const bool active = cen[tile] > 0 || cen[by * c.tiles_x + l] > 0 || cen[by * c.tiles_x + rr] > 0 ||
-                                        cen[d * c.tiles_x + bx] > 0 || cen[u * c.tiles_x + bx] > 0;
-                    need = active || !B.skipped[tile];
+                    const int k0 = cen[tile], k1 = cen[by * c.tiles_x + l], k2 = cen[by * c.tiles_x + rr];
+                    const int k3 = cen[d * c.tiles_x + bx], k4 = cen[u * c.tiles_x + bx];
+                    const bool skipped = B.skipped[tile] != 0;
+                    const bool active = (k0 > 0) | (k1 > 0) | (k2 > 0) | (k3 > 0) | (k4 > 0);
+                    need = active || !skipped;
                     if (!need) cen_next[tile] = 0;
                 }
             }
@@ -937,11 +956,7 @@ __device__ __forceinline__ void compact_body(const SweConst &c, const SweBufs &B
             __syncthreads();   // rlist of this chunk stays read-only; wsum is reused below
             if (lane == 0) wsum[w] = __popc(m);
             __syncthreads();
-            if (threadIdx.x == 0) {
-                int acc = 0;
-                for (int i = 0; i < 32; ++i) { const int v = wsum[i]; wsum[i] = acc; acc += v; }
-                chunk = acc;
-            }
+            if (w == 0) warp_exclusive_scan32(wsum, lane, &chunk);
             __syncthreads();
             if (need) B.work[2 + base + wsum[w] + __popc(m & ((1u << lane) - 1u))] = tile;
             __syncthreads();
@@ -963,10 +978,13 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) { 
 // block (dense steps) each runs at most one entry and the blocks past the
 // list's end return at once; a smaller grid (sparse steps) walks the list.
 // FP32: three blocks per SM (80 registers, 73 KB of shared memory each) for
-// every variant: those with source terms or the general laws spill 20-60
-// bytes at 80 registers and are still 10-25 % faster than at two blocks.
+// every dense variant: those with source terms or the general laws spill
+// 20-60 bytes at 80 registers and are still 10-25 % faster than at two
+// blocks.  The list-walking variant runs a wave of two blocks per SM over few
+// blocks, where the sweep's latency counts: it gets the registers of two
+// blocks per SM.
 template <typename T, int BW, int SRC, bool GEN, bool WALK>
-__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? (WALK ? 2 : 3) : 1)
 step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
@@ -1024,9 +1042,39 @@ __global__ void __launch_bounds__(BW) init_kernel(SweConst c, SweBufs B) {
 
 // ------------------------------------------------------ dt (K3) and bookkeeping
 
-// Piecewise-linear hydrograph integral over [ta, tb] (constant beyond the ends).
+// Piecewise-linear hydrograph integral over [ta, tb] (constant beyond the
+// ends), summed piece by piece in knot order.  Hydrographs of up to 4 knots
+// are read into registers first, in one batch of loads (the loop then unrolls
+// on constant indices); longer ones are read knot by knot.
 __device__ inline double hydro_integral(int nk, const double *tk, const double *Qk, double ta, double tb) {
     if (nk <= 0 || !(tb > ta)) return 0.0;
+    if (nk <= 4) {
+        double t[4], q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            t[j] = j < nk ? tk[j] : 0.0;
+            q[j] = j < nk ? Qk[j] : 0.0;
+        }
+        double s = 0.0;
+        if (ta < t[0]) { double e = tb < t[0] ? tb : t[0]; s += q[0] * (e - ta); }
+        double tl = t[0], ql = q[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j + 1 < nk) {
+                tl = t[j + 1]; ql = q[j + 1];
+                double a = ta > t[j] ? ta : t[j];
+                double b = tb < t[j + 1] ? tb : t[j + 1];
+                if (b > a) {
+                    double span = t[j + 1] - t[j];
+                    double qa = q[j] + (q[j + 1] - q[j]) * ((a - t[j]) / span);
+                    double qb = q[j] + (q[j + 1] - q[j]) * ((b - t[j]) / span);
+                    s += 0.5 * (qa + qb) * (b - a);
+                }
+            }
+        }
+        if (tb > tl) { double a = ta > tl ? ta : tl; s += ql * (tb - a); }
+        return s;
+    }
     double s = 0.0;
     if (ta < tk[0]) { double e = tb < tk[0] ? tb : tk[0]; s += Qk[0] * (e - ta); }
     for (int j = 0; j + 1 < nk; ++j) {
@@ -1046,41 +1094,48 @@ template <typename T> __device__ inline double acc_value(unsigned long long bits
 template <> __device__ inline double acc_value<float>(unsigned long long bits) { return (double)__uint_as_float((unsigned)bits); }
 template <> __device__ inline double acc_value<double>(unsigned long long bits) { return __longlong_as_double((long long)bits); }
 
-template <typename T> __device__ inline double acc_value_v(const volatile unsigned long long *p) {
-    return acc_value<T>(*p);
-}
 
 // One thread.  mode 1 (commit) first commits the step that just ran, if one
 // was scheduled (n += 1, t += dt, the maxima gathered by its epilogue become
 // the current ones); mode 2 (init) takes the maxima the census kernel
 // gathered for a freshly set state; mode 0 only re-prepares.  It then forms
 // dt of the next step from Eq. 7 (FP64), clipped to t_end - t, the source
-// increment and the step coefficients.  The bookkeeping is accessed through
-// a volatile pointer, so the body also runs inside a persistent launch.
+// increment and the step coefficients.  The bookkeeping is read first, in one
+// batch of L2-coherent loads (so the body also runs inside a persistent
+// launch, after other blocks wrote it, and waits for memory once, not once per
+// field), and written back with plain stores.
 template <typename T>
 __device__ void between_body(const SweConst &c, const SweBufs &B, int mode) {
-    volatile SweDev *d = B.dev;
+    SweDev *d = B.dev;
     const int nsrc = c.nsrc;
+    const int sched = __ldcg(&d->scheduled), binding = __ldcg(&d->binding), active = __ldcg(&d->active_tiles);
+    const long long n = __ldcg(&d->n);
+    const double t0 = __ldcg(&d->t), t_end = __ldcg(&d->t_end), dt0 = __ldcg(&d->dt);
+    const double dHs0 = __ldcg(&d->dHs), inflow0 = __ldcg(&d->inflow_total);
+    const unsigned long long a0 = __ldcg(&d->acc[0]), a1 = __ldcg(&d->acc[1]), a2 = __ldcg(&d->acc[2]);
+    double vp = __ldcg(&d->vp), vs = __ldcg(&d->vs), jm = __ldcg(&d->jm);
+    double t = t0;
     bool take = mode == 2;
-    if (mode == 1 && d->scheduled) {
-        d->n = d->n + 1;
-        d->t = d->binding == 4 ? d->t_end : d->t + d->dt;  // a clipped step lands on t_end
-        d->dt_last = d->dt;
-        d->binding_last = d->binding;
-        d->inflow_total = d->inflow_total + d->dHs * ((double)nsrc * (c.dx * c.dx));
-        d->active_last = d->active_tiles;
+    if (mode == 1 && sched) {
+        t = binding == 4 ? t_end : t0 + dt0;  // a clipped step lands on t_end
+        d->n = n + 1;
+        d->t = t;
+        d->dt_last = dt0;
+        d->binding_last = binding;
+        d->inflow_total = inflow0 + dHs0 * ((double)nsrc * (c.dx * c.dx));
+        d->active_last = active;
         take = true;
     }
     if (take) {
-        d->vp = acc_value_v<T>(&d->acc[0]);
-        d->vs = acc_value_v<T>(&d->acc[1]);
-        d->jm = acc_value_v<T>(&d->acc[2]);
+        vp = acc_value<T>(a0);
+        vs = acc_value<T>(a1);
+        jm = acc_value<T>(a2);
+        d->vp = vp; d->vs = vs; d->jm = jm;
         d->acc[0] = 0ull; d->acc[1] = 0ull; d->acc[2] = 0ull;
     }
     const double h = c.dx;
     double best = INFINITY;
     int which = 3;
-    const double vp = d->vp, vs = d->vs, jm = d->jm, t = d->t, t_end = d->t_end;
     if (vp > 0.0) { double a = h / (2.0 * vp); if (a < best) { best = a; which = 0; } }
     if (vs > 0.0) { double a = h / vs; if (a < best) { best = a; which = 1; } }
     if (c.sediment_on && jm > 0.0) {

@@ -118,6 +118,19 @@ def test_fp64_parity_flood_channel_ragged_tiles(gpu, orc):
     print("fp64 flood channel worst rel Linf:", worst)
 
 
+@pytest.mark.parametrize("knots", [1, 2, 4, 7])
+def test_fp64_parity_hydrograph_knots(gpu, orc, knots):
+    """Inflow hydrographs of 1, 2, 4 (read into registers in one batch) and 7
+    (read knot by knot) knots within the first 12 s, about a step apart, so
+    the steps start before the first knot, cross knots and run past the last:
+    the source increment, hence H, and dt match the oracle per step."""
+    sc = I.flood_channel(64, dx=5.0, seed=2, peak=300.0)
+    g = I.rng(50 + knots)
+    sc.hydro_t = np.sort(g.uniform(0.5, 12.0, knots))
+    sc.hydro_Q = g.uniform(5.0, 80.0, knots)
+    _per_step_parity(gpu, orc, sc, 30, bw=128, th=32)
+
+
 @pytest.mark.parametrize("shape", [(1, 9), (9, 1), (3, 5), (4, 4), (130, 3)])
 def test_fp64_parity_tiny_and_thin_grids(gpu, orc, shape):
     ny, nx = shape
