@@ -175,6 +175,8 @@ template <typename T> struct K {  // step constants in the state precision
     T hdtc, dtc;  // FP32: dt/2 g/(2h) and dt g/(2h), the force terms' factors (unused in FP64)
 };
 
+template <typename T> struct Ar;  // precision-specific arithmetic (below)
+
 // Grass discharge (Eq. 3) gated by the Shamov velocity (Eq. 5, written as
 // |v|^6 > C_Sh^6 d50^2 H); A_J constant or from Eq. 4.
 template <typename T, bool GEN = true>
@@ -187,8 +189,7 @@ __device__ inline void grass(const SweConst &c, const K<T> &k, bool wet, T H, T 
     // GEN = false compiles only the default laws (constant A_J, m = 2)
     T AJ = (GEN && c.aj_mode == 1) ? ajn / ((k.sm1 * mm_sqrt(k.g * H)) * k.d50) : k.A_J;
     T vm = (!GEN || c.m_is_2) ? s2 : mm_pow(s2, T(0.5) * k.m_exp);
-    Jx = (AJ * vx) * vm;
-    Jy = (AJ * vy) * vm;
+    Ar<T>::scale2(AJ, vx, vy, vm, Jx, Jy);
     Ja = (AJ * vm) * mm_sqrt(s2);
 }
 
@@ -369,6 +370,21 @@ template <> struct Ar<double> {
     __device__ static inline double k6_num(const K<double> &k, double u, double d, double ratio) {
         return u + k.dt * (-(k.coef * d) * ratio);
     }
+    // both axes at once (x, y): the K4 / K6 velocities, the Grass load
+    // components
+    __device__ static inline void k4_vel(const K<double> &k, double u, double v, double dx, double dy, double den,
+                                         double &x, double &y) {
+        div2(k4_num(k, u, dx), k4_num(k, v, dy), den, x, y);
+    }
+    __device__ static inline void k6_vel(const K<double> &k, double u, double v, double dx, double dy, double q,
+                                         double den, double &x, double &y) {
+        div2(k6_num(k, u, dx, q), k6_num(k, v, dy, q), den, x, y);
+    }
+    __device__ static inline void scale2(double a, double vx, double vy, double vm, double &x, double &y) {
+        x = (a * vx) * vm;
+        y = (a * vy) * vm;
+    }
+
     // HLL fluxes of one face from the hydrostatic face depths, the normal
     // velocities and celerities, in the oracle's order of operations
     __device__ static inline void hll_face(double HL, double HR, double uL, double uR, double cL, double cR,
@@ -380,9 +396,14 @@ template <> struct Ar<double> {
     }
 };
 template <> struct Ar<float> {
+    // Pairs of the same operation on the x and y components run as one packed
+    // FP32x2 instruction (each lane rounds as the scalar operation would): the
+    // step is bound by instruction issue, and a packed instruction takes one
+    // issue slot for two results.
     __device__ static inline void div2(float a, float b, float d, float &x, float &y) {
         const float r = 1.0f / d;
-        x = a * r; y = b * r;
+        const float2 q = __fmul2_rn(make_float2(a, b), make_float2(r, r));
+        x = q.x; y = q.y;
     }
     // the median of (a, b, 0): 0 unless a and b share a sign, else the one
     // nearer zero (four min/max, no branch)
@@ -404,6 +425,20 @@ template <> struct Ar<float> {
     __device__ static inline float k4_num(const K<float> &k, float u, float d) { return fmaf(-k.hdtc, d, u); }
     __device__ static inline float k6_factor(const K<float> &k, float ratio) { return k.dtc * ratio; }
     __device__ static inline float k6_num(const K<float> &, float u, float d, float q) { return fmaf(-q, d, u); }
+    __device__ static inline void k4_vel(const K<float> &k, float u, float v, float dx, float dy, float den,
+                                         float &x, float &y) {
+        const float2 n = __ffma2_rn(make_float2(-k.hdtc, -k.hdtc), make_float2(dx, dy), make_float2(u, v));
+        div2(n.x, n.y, den, x, y);
+    }
+    __device__ static inline void k6_vel(const K<float> &, float u, float v, float dx, float dy, float q,
+                                         float den, float &x, float &y) {
+        const float2 n = __ffma2_rn(make_float2(-q, -q), make_float2(dx, dy), make_float2(u, v));
+        div2(n.x, n.y, den, x, y);
+    }
+    __device__ static inline void scale2(float a, float vx, float vy, float vm, float &x, float &y) {
+        const float2 j = __fmul2_rn(__fmul2_rn(make_float2(a, a), make_float2(vx, vy)), make_float2(vm, vm));
+        x = j.x; y = j.y;
+    }
     // HLL with the bounds clamped to sL <= 0 <= sR: the same flux in all three
     // cases (sL >= 0 gives F_L, sR <= 0 gives F_R), so no branch.  With the
     // advective fluxes F = U u it is F = U_L alpha + U_R beta,
@@ -620,7 +655,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
                 const T cf = Ar<T>::manning(gn2, Hc);
                 const T va = mm_sqrt(u * u + v * v);
                 const T den = T(1) + k.hdt * (cf * va);
-                Ar<T>::div2(Ar<T>::k4_num(k, u, dx2), Ar<T>::k4_num(k, v, dy2), den, vtx, vty);
+                Ar<T>::k4_vel(k, u, v, dx2, dy2, den, vtx, vty);
                 // K5: forces at t_{n+1/2} from H^{n+1/2} + b, wet flags of t_n
                 const T hc = q4<P, 2>(S.hj)[o].x, ech = hc + bc;
                 const T hE = q4<P, 2>(S.hj)[o + 1].x, hW = q4<P, 2>(S.hj)[o - 1].x;
@@ -631,7 +666,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
                 // K6: corrector (Lagrangian end) velocity, Manning at |vt|
                 const T vat = mm_sqrt(vtx * vtx + vty * vty);
                 const T den2 = T(1) + k.dt * (cf * vat);
-                Ar<T>::div2(Ar<T>::k6_num(k, u, dx5, q), Ar<T>::k6_num(k, v, dy5, q), den2, wxv, wyv);
+                Ar<T>::k6_vel(k, u, v, dx5, dy5, q, den2, wxv, wyv);
                 grass<T, GEN>(c, k, true, Hc, ajo, vtx, vty, jx, jy, ja);
             }
             q4<P, 2>(S.U)[o] = V2<T>{vtx, vty};
@@ -705,7 +740,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
             T G[4] = {T(0), T(0), T(0), T(0)};
             if (need) {
                 const T e0 = H0 + b0;
-                T lo, hi, lo2, hi2;
+                T lo, hi, lo2;
                 // x direction: (H, eta, ux, wx, wy) at t-1, t, t+1
                 const V2<T> U3m = q4<P, 3>(S.U)[o - 1], U3 = q4<P, 3>(S.U)[o], U3p = q4<P, 3>(S.U)[o + 1];
                 const V2<T> W3m = q4<P, 3>(S.W)[o - 1], W3 = q4<P, 3>(S.W)[o], W3p = q4<P, 3>(S.W)[o + 1];
