@@ -231,9 +231,14 @@ swe_status swe_step_noalloc(const swe_params *p, double manning_n, void *state_i
  * grids. */
 typedef struct swe_ensemble swe_ensemble;
 
-/* n scenarios, params[k] for scenario k (all SWE_FP32, same block_cols and
- * tile_rows; 0 = library defaults).  Each scenario is a solver handle created
- * on the ensemble's stream (NULL: a private stream). */
+/* Most scenarios in one ensemble (the scenario table travels in the
+ * persistent launch's parameters). */
+#define SWE_ENSEMBLE_MAX 64
+
+/* n scenarios (1 <= n <= SWE_ENSEMBLE_MAX, else SWE_EINVAL), params[k] for
+ * scenario k (all SWE_FP32, same block_cols and tile_rows; 0 = library
+ * defaults).  Each scenario is a solver handle created on the ensemble's
+ * stream (NULL: a private stream). */
 swe_status swe_ensemble_create(int n, const swe_params *params, void *cuda_stream, swe_ensemble **out);
 swe_status swe_ensemble_destroy(swe_ensemble *e);
 
@@ -242,11 +247,12 @@ swe_status swe_ensemble_destroy(swe_ensemble *e);
 swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member);
 
 /* Advances every scenario by nsteps steps of its own Eq. 7 dt (no t_end clip)
- * in one persistent launch.  Work items (scenario, block) are scheduled by
- * dataflow: a scenario's next step starts as soon as its own previous step
- * is complete, with no barrier across scenarios.  Every scenario's state must
- * be set.  SWE_ETIMEOUT if a block's wait for a scenario's step gave up (see
- * set_timeout). */
+ * in one persistent launch.  The launch's blocks form one group per scenario,
+ * sized so that the scenarios' steps take about as long; a group runs its
+ * scenario's (step, block) items by dataflow: the scenario's next step starts
+ * as soon as its own previous step is complete, with no barrier across
+ * scenarios.  Every scenario's state must be set.  SWE_ETIMEOUT if a block's
+ * wait for a scenario's step gave up (see set_timeout). */
 swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
 
 /* Times each candidate block shape (128 or 256 columns x 16..192 rows) for

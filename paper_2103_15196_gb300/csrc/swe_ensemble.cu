@@ -4,26 +4,35 @@
 //
 // Each scenario is an ordinary solver handle (swe_create): its state, Manning
 // field, sources and diagnostics are set and read with the usual calls.  The
-// persistent kernel schedules a flattened list of (scenario, block) work
-// items by dataflow, with no grid-wide barrier:
-//   * blocks draw (step, item) pairs in order from one counter, step-major;
-//   * an item of scenario k at step n waits (bounded) until scenario k has
-//     completed n steps in this launch -- other scenarios never hold it up,
-//     since each keeps its own dt (its own K3) and time;
+// persistent kernel schedules (step, block) work items by dataflow, with no
+// grid-wide barrier:
+//   * the launch's blocks are split into one group per scenario, sized on the
+//     host so that the scenarios' steps take about as long (each further block
+//     goes to the scenario with the most grid blocks per launch block);
+//   * a group draws the (step, block) items of its scenario in order from the
+//     scenario's counter, step-major; an item of step n waits (bounded) until
+//     the scenario has completed n steps in this launch -- other scenarios
+//     never hold it up, since each keeps its own dt (its own K3) and time;
 //   * each item runs the same per-block step as the single-grid kernel (K1
 //     skip, K2-K8, census and Eq. 7 maxima) and counts itself done; the block
-//     that completes scenario k's step commits it and forms k's next dt, then
-//     publishes the step count.
-// Items are drawn in increasing order and an item only waits for items drawn
-// before it, so the earliest unfinished item can always run: the schedule
-// cannot deadlock.  Every wait polls %globaltimer with a time limit; on expiry
-// the kernel sets a status bit, every block returns, the host reads
-// SWE_ETIMEOUT, and the context stays usable.
+//     that completes the scenario's step commits it and forms the next dt,
+//     then publishes the step count.
+// A block's scenario follows from its index, so the scenario's constants and
+// buffer pointers are read from the launch parameters (the scenario table
+// travels in them, about 29 KB for 64 scenarios) at an offset that is the
+// same for the whole block: the sweep gets them as it gets the single-grid
+// kernel's constants, and fits the register budget of three blocks per SM.
+// Items are drawn in increasing order within a scenario and an item only
+// waits for items of its scenario drawn before it, which running blocks hold,
+// so the schedule cannot deadlock.  Every wait polls %globaltimer with a time
+// limit; on expiry the kernel sets a status bit, every block returns, the
+// host reads SWE_ETIMEOUT, and the context stays usable.
 //
 // An autotuner (swe_ensemble_autotune) times each candidate block shape on
 // the ensemble's own states and keeps the fastest.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <vector>
 
@@ -47,45 +56,59 @@ __device__ inline unsigned long long global_ns() {
 }
 
 // Layout of the launch's synchronisation words (zeroed before every launch):
-// [0] the (step, item) counter, [1] unused, [2] status, then per scenario k
-// done[k] = ENS_SYNC + 2k (items of its current step completed) and
-// steps[k] = ENS_SYNC + 2k + 1 (steps completed in this launch).
+// [2] status, then per scenario k: ENS_SYNC + 3k its (step, block) counter,
+// + 1 the items of its current step completed, + 2 the steps completed in
+// this launch.
 #define ENS_SYNC 4
+#define ENS_WORDS(n) (ENS_SYNC + 3 * (size_t)(n))
+
+// The launch parameters: the scenario table and the block groups (scenario k
+// owns blocks pre[k] .. pre[k + 1] - 1).
+struct EnsParams {
+    EnsScen scen[SWE_ENSEMBLE_MAX];
+    int pre[SWE_ENSEMBLE_MAX + 1];
+    int n, nsteps;
+    unsigned extra;   // completions each scenario step waits for beyond its items (> 0 only in a test)
+    unsigned *sync;
+    unsigned long long timeout_ns;
+};
+static_assert(sizeof(EnsParams) <= 32000, "the scenario table must fit the kernel parameters");
 
 // GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; FLD:
 // the rain and infiltration fields; the inflow is always compiled in
-// (scenarios carry inflow); two blocks per SM.  extra: completions
-// each scenario step waits for beyond its items (0; > 0 only to make the waits
-// run out in a test).
+// (scenarios carry inflow); three blocks per SM.
 template <int BW, bool GEN, bool FLD>
-__global__ void __launch_bounds__(BW, 2)
-ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items, int nitems, int nsteps,
-                unsigned *sync, unsigned extra, unsigned long long timeout_ns) {
+__global__ void __launch_bounds__(BW, 3) ensemble_kernel(const __grid_constant__ EnsParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
-    __shared__ long long s_g;
+    __shared__ unsigned s_g;
     __shared__ int s_stop;
-    volatile unsigned *vsync = sync;
-    const long long total = (long long)nsteps * nitems;
+    if ((int)blockIdx.x >= P.pre[P.n]) return;
+    int k = 0;
+    while (k + 1 < P.n && (int)blockIdx.x >= P.pre[k + 1]) ++k;
+    const EnsScen &sc = P.scen[k];
+    const unsigned ntile = (unsigned)(sc.c.tiles_x * sc.c.tiles_y);
+    const unsigned total = ntile * (unsigned)P.nsteps;
+    unsigned *cnt = P.sync + ENS_SYNC + 3 * k;
+    volatile unsigned *vsync = P.sync;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_g = (vsync[2] & SWE_STATUS_TIMEOUT) ? total : (long long)atomicAdd(sync, 1u);
+            s_g = (vsync[2] & SWE_STATUS_TIMEOUT) ? total : atomicAdd(cnt, 1u);
             s_stop = 0;
         }
         __syncthreads();
-        const long long g = s_g;
+        const unsigned g = s_g;
         if (g >= total) return;
-        const int step = (int)(g / nitems);
-        const int4 w = items[g % nitems];
-        // wait until scenario w.x has completed `step` steps of this launch
+        // wait until the scenario has completed the item's step count
         if (threadIdx.x == 0) {
-            volatile unsigned *done_steps = vsync + ENS_SYNC + 2 * w.x + 1;
-            if (*done_steps < (unsigned)step) {
+            const unsigned step = g / ntile;
+            volatile unsigned *done_steps = vsync + ENS_SYNC + 3 * k + 2;
+            if (*done_steps < step) {
                 const unsigned long long t0 = global_ns();
-                while (*done_steps < (unsigned)step) {
-                    if ((vsync[2] & SWE_STATUS_TIMEOUT) || global_ns() - t0 > timeout_ns) {
-                        atomicOr(sync + 2, SWE_STATUS_TIMEOUT);
+                while (*done_steps < step) {
+                    if ((vsync[2] & SWE_STATUS_TIMEOUT) || global_ns() - t0 > P.timeout_ns) {
+                        atomicOr(P.sync + 2, SWE_STATUS_TIMEOUT);
                         s_stop = 1;
                         break;
                     }
@@ -96,24 +119,20 @@ ensemble_kernel(const EnsScen *__restrict__ scen, const int4 *__restrict__ items
         }
         __syncthreads();
         if (s_stop) return;
-        step_tile<float, BW, true, SWE_SRC_INFLOW | (FLD ? SWE_SRC_FIELDS : 0), GEN>(scen[w.x].c, scen[w.x].B, w.y, w.z, S);
+        const unsigned tile = g % ntile;
+        step_tile<float, BW, true, SWE_SRC_INFLOW | (FLD ? SWE_SRC_FIELDS : 0), GEN>(
+            sc.c, sc.B, (int)(tile % (unsigned)sc.c.tiles_x), (int)(tile / (unsigned)sc.c.tiles_x), S);
         __syncthreads();
         if (threadIdx.x == 0) {
-            // the item again from shared memory: nothing of it need stay in a
-            // register through the sweep
-            const long long g2 = s_g;
-            const int step2 = (int)(g2 / nitems);
-            const int4 w2 = items[g2 % nitems];
-            const EnsScen &sc = scen[w2.x];
+            const unsigned step = s_g / ntile;
             __threadfence();   // this item's state, census and maxima before its count
-            const unsigned target = (unsigned)(sc.c.tiles_x * sc.c.tiles_y) + extra;
-            if (atomicAdd(sync + ENS_SYNC + 2 * w2.x, 1u) + 1u == target) {
+            if (atomicAdd(cnt + 1, 1u) + 1u == ntile + P.extra) {
                 // the scenario's step is complete: commit it, form its next dt
-                atomicExch(sync + ENS_SYNC + 2 * w2.x, 0u);
+                atomicExch(cnt + 1, 0u);
                 __threadfence();
                 between_body<float>(sc.c, sc.B, 1);
                 __threadfence();
-                atomicExch(sync + ENS_SYNC + 2 * w2.x + 1, (unsigned)(step2 + 1));
+                atomicExch(cnt + 2, step + 1);
             }
         }
     }
@@ -126,15 +145,15 @@ struct swe_ensemble {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int bw = 256, th = 64;
-    EnsScen *d_scen = nullptr;
-    int4 *d_items = nullptr;
-    size_t items_cap = 0;
-    unsigned *d_sync = nullptr;  // ENS_SYNC + 2 n words: work counter, status, per-scenario counts
+    EnsParams P;                 // the launch parameters of the next run (nsteps set per launch)
+    unsigned *d_sync = nullptr;  // ENS_WORDS(n) words: status, per-scenario counters
     unsigned long long timeout_ns = 2000000000ull;
     int extra = 0;            // test hook: completions each scenario step waits for beyond its items
-    std::map<long long, cudaGraphExec_t> graphs;
-    int nitems = 0;
-    int grid = 0;            // co-resident blocks of the persistent kernel for bw
+    std::map<long long, cudaGraphExec_t> graphs;   // per step count, for the parameters in graph_P
+    EnsParams graph_P;        // the parameters (nsteps aside) the cached graphs were captured with
+    int max_tiles = 0;        // grid blocks of the largest scenario
+    int resident = 0;         // co-resident blocks of the persistent kernel variant resident_key
+    int resident_key = -1;
     bool gen = false;        // some scenario uses the general transport laws
     bool fld = false;        // some scenario has a rain or infiltration field
     bool graph_ok = true;    // false if this driver cannot capture the persistent launch
@@ -155,14 +174,39 @@ template <int BW, bool GEN, bool FLD> int resident_blocks() {
 void clear_graphs(swe_ensemble *e) {
     for (auto &g : e->graphs) cudaGraphExecDestroy(g.second);
     e->graphs.clear();
-    e->grid = 0;
 }
 
-// Uploads the scenario descriptors and the work list (scenario, bx, by).
+int resident_for(const swe_ensemble *e);
+
+// Block groups: every scenario one block, then each further block to the
+// scenario with the most grid blocks per launch block (ties: the larger
+// scenario), up to the resident blocks or every grid block its own.
+void split_blocks(const std::vector<int> &tiles, int resident, int *pre) {
+    const int n = (int)tiles.size();
+    std::vector<int> b(n, 1);
+    int used = n;
+    auto load = [&](int k) { return (tiles[k] + b[k] - 1) / b[k]; };
+    while (used < resident) {
+        int best = -1;
+        for (int k = 0; k < n; ++k) {
+            if (b[k] >= tiles[k]) continue;
+            if (best < 0 || load(k) > load(best) || (load(k) == load(best) && tiles[k] > tiles[best])) best = k;
+        }
+        if (best < 0) break;
+        ++b[best];
+        ++used;
+    }
+    pre[0] = 0;
+    for (int k = 0; k < n; ++k) pre[k + 1] = pre[k] + b[k];
+}
+
+// Gathers the scenario table and the block groups into the launch
+// parameters; the cached graphs are dropped when they change.
 swe_status upload(swe_ensemble *e) {
     const int n = (int)e->members.size();
-    std::vector<EnsScen> sc(n);
-    std::vector<int4> items;
+    EnsParams &P = e->P;
+    std::memset(&P, 0, sizeof(P));
+    std::vector<int> tiles(n);
     bool fld = false;
     for (int k = 0; k < n; ++k) {
         SweConst *c = nullptr;
@@ -171,45 +215,42 @@ swe_status upload(swe_ensemble *e) {
         handle_view(e->members[k], &c, &b, nullptr, nullptr, nullptr, &set);
         if (!set) return SWE_ESTATE;
         if (handle_free_stepping(e->members[k]) != SWE_OK) return SWE_ECUDA;
-        sc[k].c = *c;
-        sc[k].B = *b;
+        P.scen[k].c = *c;
+        P.scen[k].B = *b;
         fld = fld || c->has_rain || c->has_beta;
-        for (int by = 0; by < c->tiles_y; ++by)
-            for (int bx = 0; bx < c->tiles_x; ++bx) items.push_back(make_int4(k, bx, by, 0));
+        tiles[k] = c->tiles_x * c->tiles_y;
     }
-    if (items.size() > e->items_cap) {
-        cudaFree(e->d_items);
-        e->d_items = nullptr;
-        if (cudaMalloc(&e->d_items, items.size() * sizeof(int4)) != cudaSuccess) return SWE_ENOMEM;
-        e->items_cap = items.size();
-        clear_graphs(e);   // captured launches point at the old list
-    }
-    if ((int)items.size() != e->nitems || fld != e->fld) clear_graphs(e);   // (also resets the grid)
     e->fld = fld;
-    e->nitems = (int)items.size();
-    if (cudaMemcpyAsync(e->d_scen, sc.data(), n * sizeof(EnsScen), cudaMemcpyHostToDevice, e->stream) != cudaSuccess ||
-        cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, e->stream) !=
-            cudaSuccess)
-        return SWE_ECUDA;
+    const int key = (e->bw == 128 ? 4 : 0) | (e->gen ? 2 : 0) | (e->fld ? 1 : 0);
+    if (key != e->resident_key) {
+        e->resident = resident_for(e);
+        e->resident_key = key;
+    }
+    split_blocks(tiles, std::max(e->resident, n), P.pre);
+    P.n = n;
+    P.extra = (unsigned)e->extra;
+    P.sync = e->d_sync;
+    P.timeout_ns = e->timeout_ns;
+    e->max_tiles = *std::max_element(tiles.begin(), tiles.end());
+    if (std::memcmp(&P, &e->graph_P, sizeof(P)) != 0) {
+        clear_graphs(e);
+        e->graph_P = P;
+    }
     return SWE_OK;
 }
 
 template <int BW, bool GEN, bool FLD> cudaError_t launch_persistent(swe_ensemble *e, int nsteps) {
-    const int grid = e->grid;
     const size_t smem = sizeof(StepSmem<float, BW>);
-    const size_t words = ENS_SYNC + 2 * e->members.size();
-    cudaError_t err = cudaMemsetAsync(e->d_sync, 0, words * sizeof(unsigned), e->stream);
+    cudaError_t err = cudaMemsetAsync(e->d_sync, 0, ENS_WORDS(e->members.size()) * sizeof(unsigned), e->stream);
     if (err != cudaSuccess) return err;
+    e->P.nsteps = nsteps;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = dim3(e->P.pre[e->P.n]);
     cfg.blockDim = dim3(BW);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = e->stream;
     cfg.numAttrs = 0;   // no grid barrier: blocks need not be co-resident
-    const EnsScen *sc = e->d_scen;
-    const int4 *it = e->d_items;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN, FLD>, sc, it, e->nitems, nsteps, e->d_sync,
-                              (unsigned)e->extra, e->timeout_ns);
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<BW, GEN, FLD>, e->P);
 }
 
 int resident_for(const swe_ensemble *e) {
@@ -269,7 +310,7 @@ swe_status check(swe_ensemble *e) {
         return SWE_ECUDA;
     if (st & SWE_STATUS_TIMEOUT) {
         // clear the bit so the ensemble can be used again once the cause is fixed
-        cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * e->members.size()) * sizeof(unsigned), e->stream);
+        cudaMemsetAsync(e->d_sync, 0, ENS_WORDS(e->members.size()) * sizeof(unsigned), e->stream);
         cudaStreamSynchronize(e->stream);
         return SWE_ETIMEOUT;
     }
@@ -283,7 +324,7 @@ swe_status check(swe_ensemble *e) {
 }  // namespace
 
 extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void *cuda_stream, swe_ensemble **out) {
-    if (n < 1 || !params || !out) return SWE_EINVAL;
+    if (n < 1 || n > SWE_ENSEMBLE_MAX || !params || !out) return SWE_EINVAL;
     *out = nullptr;
     for (int k = 0; k < n; ++k)
         if (params[k].precision != SWE_FP32 || params[k].block_cols != params[0].block_cols ||
@@ -308,9 +349,8 @@ extern "C" swe_status swe_ensemble_create(int n, const swe_params *params, void 
         if (s != SWE_OK) { swe_ensemble_destroy(e); return s; }
         e->members.push_back(h);
     }
-    if (cudaMalloc(&e->d_scen, n * sizeof(EnsScen)) != cudaSuccess ||
-        cudaMalloc(&e->d_sync, (ENS_SYNC + 2 * (size_t)n) * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * (size_t)n) * sizeof(unsigned), e->stream) != cudaSuccess) {
+    if (cudaMalloc(&e->d_sync, ENS_WORDS(n) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(e->d_sync, 0, ENS_WORDS(n) * sizeof(unsigned), e->stream) != cudaSuccess) {
         swe_ensemble_destroy(e);
         return SWE_ENOMEM;
     }
@@ -323,8 +363,6 @@ extern "C" swe_status swe_ensemble_destroy(swe_ensemble *e) {
     if (e->stream) cudaStreamSynchronize(e->stream);
     clear_graphs(e);
     for (swe_handle *h : e->members) swe_destroy(h);
-    cudaFree(e->d_scen);
-    cudaFree(e->d_items);
     cudaFree(e->d_sync);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
@@ -343,11 +381,9 @@ extern "C" swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps) {
     if (nsteps == 0) return SWE_OK;
     swe_status s = upload(e);
     if (s != SWE_OK) return s;
-    if (e->grid == 0)
-        e->grid = resident_for(e);
-    // one persistent launch per call (split only where steps x items would
-    // overflow the 32-bit work counter)
-    const int64_t max_chunk = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max(1, e->nitems));
+    // one persistent launch per call (split only where steps x blocks of a
+    // scenario would overflow its 32-bit work counter)
+    const int64_t max_chunk = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max(1, e->max_tiles));
     while (nsteps > 0) {
         const int chunk = (int)std::min<int64_t>(nsteps, max_chunk);
         cudaGraphExec_t g;
@@ -368,7 +404,7 @@ extern "C" swe_status swe_ensemble_set_timeout(swe_ensemble *e, double seconds, 
     e->timeout_ns = (unsigned long long)(seconds * 1e9);
     e->extra = extra_arrivals;
     clear_graphs(e);
-    if (cudaMemsetAsync(e->d_sync, 0, (ENS_SYNC + 2 * e->members.size()) * sizeof(unsigned), e->stream) != cudaSuccess)
+    if (cudaMemsetAsync(e->d_sync, 0, ENS_WORDS(e->members.size()) * sizeof(unsigned), e->stream) != cudaSuccess)
         return SWE_ECUDA;
     return SWE_OK;
 }

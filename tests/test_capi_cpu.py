@@ -49,6 +49,18 @@ def test_create_rejects_bad_params_before_touching_the_device():
         assert L.swe_create(ctypes.byref(q), None, ctypes.byref(h)) == swe.SWE_EINVAL, side
 
 
+def test_ensemble_create_rejects_counts_outside_its_table_before_touching_the_device():
+    """An ensemble holds 1 .. SWE_ENSEMBLE_MAX (64) scenarios: its scenario
+    table travels in the persistent launch's parameters."""
+    L = swe.load_library()
+    p = swe.Params()
+    L.swe_params_default(ctypes.byref(p), 8, 8, 1.0)
+    arr = (swe.Params * 65)(*([p] * 65))
+    e = ctypes.c_void_p()
+    for n in (0, 65):
+        assert L.swe_ensemble_create(n, arr, None, ctypes.byref(e)) == swe.SWE_EINVAL, n
+
+
 def test_boundary_kinds_default_to_walls_and_map_by_side():
     L = swe.load_library()
     p = swe.Params()
