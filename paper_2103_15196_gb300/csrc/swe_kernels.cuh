@@ -500,8 +500,8 @@ __device__ inline void face_flux2(const SweConst &c, const K<T> &k, const T L[5]
 // register for both).
 template <typename T, bool GEN = true>
 __device__ inline void cell_epilogue2(const SweConst &c, const K<T> &k, T hn, T hun, T hvn, T bn, T ajn,
-                                      bool src, unsigned &cnt, T &m0, T &m1, T &m2) {
-    const bool wet = is_wet(hn, c);
+                                      bool src, unsigned &cnt, T &m0, T &m1, T &m2, T epsw) {
+    const bool wet = hn > epsw;
     cnt += (wet || src) ? 1u : 0u;
     if (wet) {
         T u, v;
@@ -570,6 +570,8 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
     int asy, bsy;
     V2<T> *hbk[4];          // 2-row banks of the 8-row (H, b) ring holding rows 2m-2j, 2m-2j+1
     int q4c, q4o;           // offsets of the current / previous 2-row bank of the 4-row rings
+    T epsw;                 // the wet threshold (is_wet), held in a register in the persistent launch
+    __device__ __forceinline__ bool wet_cell(T H) const { return H > epsw; }
 
     // Ring row r lives in slot r mod 8 (H, b) or r mod 4 (the 4-row rings).
     // For a sweep position s = 2m + P, row s-D = 2m + d with d = P - D, i.e.
@@ -615,7 +617,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
                 const int yy = reflect(s + 2, c.ny, c.bc[2], c.bc[3], bsy);
                 if (SWE_IN((long long)yy * c.nx + xx, SWE_NCELL)) load_cell((long long)yy * c.nx + xx, bH, bHu, bHv, bb0);
             }
-            const bool wet = is_wet(H, c);
+            const bool wet = wet_cell(H);
             HB<P, 0>()[o] = V2<T>{H, bb};
             T u = T(0);
             if (wet) Ar<T>::div2(sxT * Hu, syT * Hv, H, u, v_s);
@@ -632,7 +634,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
             const int r = s - 2;
             const V2<T> C = HB<P, 2>()[o];
             const T Hc = C.x;
-            const bool wet = is_wet(Hc, c);
+            const bool wet = wet_cell(Hc);
             T vtx = T(0), vty = T(0), wxv = T(0), wyv = T(0), jx = T(0), jy = T(0), ja = T(0);
             if (wet) {
                 const T bc = C.y, u = q4<P, 2>(S.u)[o], v = vB[P];
@@ -646,7 +648,7 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
                 const V2<T> E = HB<P, 2>()[o + 1], Wc = HB<P, 2>()[o - 1];
                 const V2<T> N = HB<P, 1>()[o], Sc = HB<P, 3>()[o];
                 const T HE = E.x, bE = E.y, HW = Wc.x, bW = Wc.y, HN = N.x, bN = N.y, HS = Sc.x, bS = Sc.y;
-                const bool wE = is_wet(HE, c), wW = is_wet(HW, c), wN = is_wet(HN, c), wS = is_wet(HS, c);
+                const bool wE = wet_cell(HE), wW = wet_cell(HW), wN = wet_cell(HN), wS = wet_cell(HS);
                 // K2: forces at t_n (free-surface differences per axis)
                 const T ec = Hc + bc;
                 const T dx2 = axis_diff<T>(ec, HE + bE, bE, wE, HW + bW, bW, wW);
@@ -704,20 +706,20 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
                     hvn = hvn * ratio;
                 }
             }
-            if (!is_wet(hn, c)) { hun = T(0); hvn = T(0); }
+            if (!wet_cell(hn)) { hun = T(0); hvn = T(0); }
             const T bn = bc - k.cb * ((f.d - fw.d) + dG[3]);
             if (SWE_IN((long long)r * c.nx + x, SWE_NCELL)) CellIO<T>::store(out, (long long)r * c.nx + x, hn, hun, hvn, bn);
             if (GEN && c.aj_mode == 1 && (r >> c.man_shift) != aj_row && SWE_IN((r >> c.man_shift) * c.man_w + mcol, SWE_NMAN)) {
                 aj_row = r >> c.man_shift;
                 aj_out = tab<T>(B.ajn, aj_row * c.man_w + mcol);
             }
-            cell_epilogue2<T, GEN>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2);
+            cell_epilogue2<T, GEN>(c, k, hn, hun, hvn, bn, aj_out, src, cnt, m0, m1, m2, epsw);
         }
         // ---------------- x-faces of row s-4 (face t|t+1): own plus-face state
         // (from the previous position) and the minus-face state of t+1
         if (FULL || (s - 4 >= y0 && s - 4 <= y1 - 1)) {
             const V2<T> C = HB<P, 4>()[o], E = HB<P, 4>()[o + 1];
-            const bool wc = is_wet(C.x, c), we = is_wet(E.x, c);
+            const bool wc = wet_cell(C.x), we = wet_cell(E.x);
             T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
             if (wc || we) {
                 const V4<T> q = S.qw[PM4_2][o + 1];
@@ -735,8 +737,8 @@ template <typename T, int BW, bool COHERENT, int SRC, bool GEN> struct Sweep {
             const V2<T> C = HB<P, 3>()[o], Wc = HB<P, 3>()[o - 1], E = HB<P, 3>()[o + 1];
             const V2<T> Sc = HB<P, 4>()[o], N = HB<P, 2>()[o];
             const T H0 = C.x, b0 = C.y, Hm = Wc.x, Hp = E.x, Hs = Sc.x, Hn = N.x;
-            const bool w0 = is_wet(H0, c), ws = is_wet(Hs, c);
-            const bool need = w0 || ws || is_wet(Hm, c) || is_wet(Hp, c) || is_wet(Hn, c);
+            const bool w0 = wet_cell(H0), ws = wet_cell(Hs);
+            const bool need = w0 || ws || wet_cell(Hm) || wet_cell(Hp) || wet_cell(Hn);
             T G[4] = {T(0), T(0), T(0), T(0)};
             if (need) {
                 const T e0 = H0 + b0;
@@ -846,6 +848,14 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     w.sxT = T(sx);
     w.mcol = w.xx >> c.man_shift;
     w.out_lane = (t >= 4) && (t < BW - 4) && (w.x < c.nx);
+    if constexpr (sizeof(T) == 4) {
+        // a persistent launch reads the scenario's threshold at a block-uniform
+        // parameter offset; the move keeps one register copy for the sweep
+        if (COHERENT) asm volatile("mov.b32 %0, %1;" : "=f"(w.epsw) : "f"(c.eps_f));
+        else w.epsw = c.eps_f;
+    } else {
+        w.epsw = T(c.eps);
+    }
     w.o = t + 2;                                     // padded smem index
     w.gn2_row = -1; w.aj_row = -1;
     w.gn2 = T(0); w.ajo = T(0); w.aj_out = T(0);
