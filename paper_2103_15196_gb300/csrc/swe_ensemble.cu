@@ -9,19 +9,25 @@
 //   * the launch's blocks are split into one group per scenario, sized on the
 //     host so that the scenarios' steps take about as long (each further block
 //     goes to the scenario with the most grid blocks per launch block);
-//   * a group draws the (step, block) items of its scenario in order from the
-//     scenario's counter, step-major; an item of step n waits (bounded) until
-//     the scenario has completed n steps in this launch -- other scenarios
-//     never hold it up, since each keeps its own dt (its own K3) and time;
+//   * a block draws the (step, block) items of its group's scenario in order
+//     from the scenario's counter, step-major, while that scenario's next item
+//     belongs to a step already open; otherwise (the scenario's current step
+//     is all drawn, or all its steps are) it draws an open item of another
+//     scenario, the one with the most items left per block of its group, so
+//     that no block idles while any scenario has work it could start;
+//   * an item of step n waits (bounded) until its scenario has completed n
+//     steps in this launch -- other scenarios never hold it up, since each
+//     keeps its own dt (its own K3) and time;
 //   * each item runs the same per-block step as the single-grid kernel (K1
 //     skip, K2-K8, census and Eq. 7 maxima) and counts itself done; the block
 //     that completes the scenario's step commits it and forms the next dt,
 //     then publishes the step count.
-// A block's scenario follows from its index, so the scenario's constants and
-// buffer pointers are read from the launch parameters (the scenario table
-// travels in them, about 29 KB for 64 scenarios) at an offset that is the
-// same for the whole block: the sweep gets them as it gets the single-grid
-// kernel's constants, and fits the register budget of three blocks per SM.
+// An item's scenario is the same for the whole block, so the scenario's
+// constants and buffer pointers are read from the launch parameters (the
+// scenario table travels in them, about 29 KB for 64 scenarios) at an offset
+// that is the same for the whole block: the sweep gets them as it gets the
+// single-grid kernel's constants, and fits the register budget of three
+// blocks per SM.
 // Items are drawn in increasing order within a scenario and an item only
 // waits for items of its scenario drawn before it, which running blocks hold,
 // so the schedule cannot deadlock.  Every wait polls %globaltimer with a time
@@ -82,24 +88,74 @@ __global__ void __launch_bounds__(BW, 3) ensemble_kernel(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
     __shared__ unsigned s_g;
-    __shared__ int s_stop;
+    __shared__ int s_k, s_stop;
     if ((int)blockIdx.x >= P.pre[P.n]) return;
-    int k = 0;
-    while (k + 1 < P.n && (int)blockIdx.x >= P.pre[k + 1]) ++k;
-    const EnsScen &sc = P.scen[k];
-    const unsigned ntile = (unsigned)(sc.c.tiles_x * sc.c.tiles_y);
-    const unsigned total = ntile * (unsigned)P.nsteps;
-    unsigned *cnt = P.sync + ENS_SYNC + 3 * k;
+    int own = 0;   // the block's group
+    while (own + 1 < P.n && (int)blockIdx.x >= P.pre[own + 1]) ++own;
     volatile unsigned *vsync = P.sync;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            s_g = (vsync[2] & SWE_STATUS_TIMEOUT) ? total : atomicAdd(cnt, 1u);
-            s_stop = 0;
+        if (threadIdx.x < 32) {
+            // Warp 0 draws the block's next item: one of its own scenario
+            // while that scenario's next item belongs to a step already open;
+            // otherwise an open item of the scenario with the most items left
+            // per block of its group (the lanes examine the scenarios together,
+            // two each, and agree on the largest key); with no open item
+            // anywhere, its own scenario's next item (waited for below), or,
+            // once its own items are all drawn, that scenario's.  So blocks do
+            // not idle at the end of their scenario's steps, nor once their
+            // scenario has finished.
+            const int lane = (int)threadIdx.x;
+            int kk = -1;
+            unsigned gg = 0;
+            for (int tries = 0; tries <= P.n && kk < 0 && !(vsync[2] & SWE_STATUS_TIMEOUT); ++tries) {
+                const unsigned ntk = (unsigned)(P.scen[own].c.tiles_x * P.scen[own].c.tiles_y);
+                const unsigned ck = vsync[ENS_SYNC + 3 * own];
+                const bool own_left = ck < ntk * (unsigned)P.nsteps;
+                const bool own_open = own_left && vsync[ENS_SYNC + 3 * own + 2] >= ck / ntk;
+                int pick = own;
+                if (!own_open) {
+                    // key: open (bit 63) | valid (bit 62) | items left per group block << 6 | scenario
+                    unsigned long long key = 0;
+                    for (int j = lane; j < P.n; j += 32) {
+                        const unsigned nt = (unsigned)(P.scen[j].c.tiles_x * P.scen[j].c.tiles_y);
+                        const unsigned tot = nt * (unsigned)P.nsteps;
+                        const unsigned c0 = vsync[ENS_SYNC + 3 * j];
+                        if (c0 >= tot) continue;
+                        const bool open = vsync[ENS_SYNC + 3 * j + 2] >= c0 / nt;
+                        const unsigned long long rem =
+                            ((unsigned long long)(tot - c0) << 16) / (unsigned)(P.pre[j + 1] - P.pre[j]);
+                        const unsigned long long kj =
+                            ((unsigned long long)open << 63) | (1ull << 62) | (rem << 6) | (unsigned long long)j;
+                        key = kj > key ? kj : key;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+                        key = y > key ? y : key;
+                    }
+                    if (key == 0) break;   // every scenario's items are drawn
+                    if ((key >> 63) || !own_left) pick = (int)(key & 63ull);
+                }
+                const unsigned ntp = (unsigned)(P.scen[pick].c.tiles_x * P.scen[pick].c.tiles_y);
+                unsigned v = 0;
+                if (lane == 0) v = atomicAdd(P.sync + ENS_SYNC + 3 * pick, 1u);
+                gg = __shfl_sync(0xffffffffu, v, 0);
+                if (gg < ntp * (unsigned)P.nsteps) kk = pick;
+            }
+            if (lane == 0) {
+                s_k = kk;
+                s_g = gg;
+                s_stop = 0;
+            }
         }
         __syncthreads();
+        const int k = s_k;   // the item's scenario
+        if (k < 0) return;
+        const EnsScen &sc = P.scen[k];
+        const unsigned ntile = (unsigned)(sc.c.tiles_x * sc.c.tiles_y);
+        unsigned *cnt = P.sync + ENS_SYNC + 3 * k;
         const unsigned g = s_g;
-        if (g >= total) return;
         // wait until the scenario has completed the item's step count
         if (threadIdx.x == 0) {
             const unsigned step = g / ntile;
@@ -124,7 +180,7 @@ __global__ void __launch_bounds__(BW, 3) ensemble_kernel(const __grid_constant__
             sc.c, sc.B, (int)(tile % (unsigned)sc.c.tiles_x), (int)(tile / (unsigned)sc.c.tiles_x), S);
         __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned step = s_g / ntile;
+            const unsigned step = g / ntile;
             __threadfence();   // this item's state, census and maxima before its count
             if (atomicAdd(cnt + 1, 1u) + 1u == ntile + P.extra) {
                 // the scenario's step is complete: commit it, form its next dt

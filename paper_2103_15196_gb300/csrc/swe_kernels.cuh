@@ -866,21 +866,33 @@ __device__ __forceinline__ void step_tile(const SweConst &c, const SweBufs &B, i
     w.vA[0] = w.vA[1] = T(0);
     w.iA[0] = w.iA[1] = T(0);
     w.cnt = 0u; w.m0 = T(0); w.m1 = T(0); w.m2 = T(0);
-    {
+    // A warp whose columns all lie more than 4 past the grid (in the last
+    // column band) feeds no output cell: the one step of an output cell
+    // reaches 4 columns, and the 4th of them only through its loaded state.
+    // In the persistent ensemble launch (COHERENT), where the grids are small
+    // and last bands common, such a warp takes part in the barriers and
+    // nothing else; the live column next to it reads its never-written ring
+    // slots only for values that feed no output (as at the block's own
+    // edge).  The single-grid kernel computes them (at 16384^2 they are 1.3 %
+    // of the work, and the branch around the sweep made that kernel slower).
+    const bool live = COHERENT ? (tx0 - 4 + (t & ~31) < c.nx + 4) : true;
+    if (!live) {
+        for (int s = y0 - 8; s <= y1 + 4; s += 2) { __syncthreads(); __syncthreads(); }
+    } else {
         int yy = reflect(y0 - 4, c.ny, c.bc[2], c.bc[3], w.asy);
         if (SWE_IN((long long)yy * c.nx + w.xx, SWE_NCELL)) w.load_cell((long long)yy * c.nx + w.xx, w.aH, w.aHu, w.aHv, w.ab);
         yy = reflect(y0 - 3, c.ny, c.bc[2], c.bc[3], w.bsy);
         if (SWE_IN((long long)yy * c.nx + w.xx, SWE_NCELL)) w.load_cell((long long)yy * c.nx + w.xx, w.bH, w.bHu, w.bHv, w.bb0);
-    }
-    // sweep positions y0-8 .. y1+4 in pairs (y0 is a multiple of 8)
-    for (int s = y0 - 8; s <= y1 + 4; s += 2) {
-        w.set_banks(s);
-        if (s >= y0 + 5 && s + 1 <= y1 + 3) {
-            w.template pos<0, true>(s);
-            w.template pos<1, true>(s + 1);
-        } else {
-            w.template pos<0, false>(s);
-            w.template pos<1, false>(s + 1);
+        // sweep positions y0-8 .. y1+4 in pairs (y0 is a multiple of 8)
+        for (int s = y0 - 8; s <= y1 + 4; s += 2) {
+            w.set_banks(s);
+            if (s >= y0 + 5 && s + 1 <= y1 + 3) {
+                w.template pos<0, true>(s);
+                w.template pos<1, true>(s + 1);
+            } else {
+                w.template pos<0, false>(s);
+                w.template pos<1, false>(s + 1);
+            }
         }
     }
     block_finish<T, BW>((int)(w.cnt & 0xffffffu), w.m0, w.m1, w.m2, w.cnt >> 24, tile, cen_out, dev, 1);
