@@ -500,7 +500,7 @@ extern "C" swe_status swe_ensemble_autotune(swe_ensemble *e, int trial_steps, in
         return SWE_OK;
     };
     const int cand_bw[2] = {128, 256};
-    const int cand_th[6] = {16, 32, 64, 96, 128, 192};
+    const int cand_th[7] = {16, 32, 64, 96, 128, 192, 256};
     float best = INFINITY;
     int best_bw = e->bw, best_th = e->th;
     cudaEvent_t e0, e1;
