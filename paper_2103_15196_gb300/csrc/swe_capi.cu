@@ -170,12 +170,17 @@ extern "C" swe_status swe_create(const swe_params *pp, void *cuda_stream, swe_ha
         h->own_stream = true;
     }
     h->cell_bytes = is_f32(h) ? 16 : 32;
-    // block shape: BW threads = columns (BW-8 written), th rows per strip
+    // block shape: BW threads = columns (BW-8 written), th rows per strip.
+    // Default width, measured on GB300 (FP32, half-wet terrain): 128 columns
+    // from 2^25 cells (six blocks per SM: 16384^2 59.2 against 58.3 Gcell/s,
+    // 8192^2 53.8 against 52.5), 256 below (4096^2 and 2048^2 have fewer
+    // 128-column blocks than resident slots), 128 on grids of at most 120
+    // columns
     long long ncell = (long long)p.nx * p.ny;
-    h->bw = p.block_cols ? p.block_cols : (p.nx <= 120 ? 128 : 256);
+    h->bw = p.block_cols ? p.block_cols : ((p.nx <= 120 || ncell >= (1ll << 25)) ? 128 : 256);
     int th = p.tile_rows;
     // default strip height, measured on GB300 (FP32, half-wet terrain): 256
-    // rows from 2^28 cells, 128 from 2^25 (8192^2: 48.9 Gcell/s against 46.1
+    // rows from 2^28 cells, 128 from 2^25 (8192^2: 53.8 Gcell/s against 51.9
     // at 256), 64 from 2^22, 32 below
     if (th == 0) th = ncell >= (1ll << 28) ? 256 : (ncell >= (1ll << 25) ? 128 : (ncell >= (1ll << 22) ? 64 : 32));
     SweConst &c = h->c;

@@ -82,9 +82,10 @@ static_assert(sizeof(EnsParams) <= 32000, "the scenario table must fit the kerne
 
 // GEN: compile the general transport laws (A_J from Eq. 4, m != 2) in; FLD:
 // the rain and infiltration fields; the inflow is always compiled in
-// (scenarios carry inflow); three blocks per SM.
+// (scenarios carry inflow); 24 warps per SM (three 256-thread or six
+// 128-thread blocks).
 template <int BW, bool GEN, bool FLD>
-__global__ void __launch_bounds__(BW, 3) ensemble_kernel(const __grid_constant__ EnsParams P) {
+__global__ void __launch_bounds__(BW, BW == 128 ? 6 : 3) ensemble_kernel(const __grid_constant__ EnsParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<float, BW> &S = *reinterpret_cast<StepSmem<float, BW> *>(smem_raw);
     __shared__ unsigned s_g;

@@ -1034,14 +1034,18 @@ __global__ void __launch_bounds__(1024) compact_kernel(SweConst c, SweBufs B) { 
 // (a column band x row strip each).  Launched with one CUDA block per grid
 // block (dense steps) each runs at most one entry and the blocks past the
 // list's end return at once; a smaller grid (sparse steps) walks the list.
-// FP32: three blocks per SM (80 registers, 73 KB of shared memory each) for
-// every dense variant: those with source terms or the general laws spill
-// 20-60 bytes at 80 registers and are still 10-25 % faster than at two
-// blocks.  The list-walking variant runs a wave of two blocks per SM over few
+// FP32: 24 warps per SM at 80 registers for every dense variant: three
+// 256-column blocks (73 KB of shared memory each) or six 128-column blocks
+// (37 KB each), whose barriers wait for 4 warps instead of 8 (on grids of
+// 2^25 cells and more 1.6-2.3 % faster than the 256-column blocks despite
+// twice the halo columns; on smaller grids, with fewer blocks than resident
+// slots, slower).  The variants with source terms or the general laws spill
+// 20-60 bytes at 80 registers and are still 10-25 % faster than at 16 warps
+// per SM.  The list-walking variant runs a wave of two blocks per SM over few
 // blocks, where the sweep's latency counts: it gets the registers of two
 // blocks per SM.
 template <typename T, int BW, int SRC, bool GEN, bool WALK>
-__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? (WALK ? 2 : 3) : 1)
+__global__ void __launch_bounds__(BW, sizeof(T) == 4 ? (WALK ? 2 : (BW == 128 ? 6 : 3)) : 1)
 step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);

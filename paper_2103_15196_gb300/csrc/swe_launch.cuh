@@ -16,7 +16,8 @@ template <typename T> size_t step_smem_bytes(int bw) {
 // it), then one CUDA block per grid block, the unlisted ones returning at
 // once.  The kernel variant compiles only the terms in use: the inflow, and
 // the rain and infiltration fields (SRC bits), the general transport laws
-// (GEN); every FP32 variant runs three blocks per SM.
+// (GEN); every dense FP32 variant runs 24 warps per SM (three 256-column or
+// six 128-column blocks).
 template <typename T, int BW, int SRC, bool GEN>
 static cudaError_t launch_step_v(const SweConst &c, const SweBufs &b, cudaStream_t s, int grid, bool list) {
     // the shared-memory opt-in is a per-device function attribute: one bit
