@@ -190,12 +190,14 @@ def test_fp64_parity_options(gpu, orc, opts):
     print("fp64 options", opts, "worst rel Linf:", worst)
 
 
+@pytest.mark.parametrize("bw", [256, 128])
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)], ids=["walls", "open"])
-def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc):
+def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc, bw):
     """FP32 state, element by element against the FP64 oracle one step at a
-    time from the same inputs, on a 333 x 271 grid (2 x 9 blocks of 248 x 32
-    with ragged right and bottom edges), walls or open sides: the per-step
-    FP32 bound of the full-size test (4e-5 m on H and b, 4e-5 m^2/s +
+    time from the same inputs, on a 333 x 271 grid (2 x 9 blocks of 248 x 32,
+    or 3 x 9 of 120 x 32 -- the kernels compiled for three and for six blocks
+    per SM -- with ragged right and bottom edges), walls or open sides: the
+    per-step FP32 bound of the full-size test (4e-5 m on H and b, 4e-5 m^2/s +
     2e-5 |Hu| on momenta)."""
     nx, ny = 333, 271
     side = max(nx, ny)
@@ -203,7 +205,7 @@ def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc):
     H, b = base.H[:ny, :nx].astype(np.float64), base.b[:ny, :nx].astype(np.float64)
     Hu, Hv = 0.5 * H, -0.3 * H          # a drift across every side, so the boundaries matter
     sides = dict(bc_w=bc[0], bc_e=bc[1], bc_s=bc[2], bc_n=bc[3])
-    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32, **sides)
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=bw, tile_rows=32, **sides)
     S.set_manning(np.full((ny, nx), 0.035), block=0)
     S.set_state(H, Hu, Hv, b)
     p = orc.Params(nx=nx, ny=ny, dx=base.dx, **sides)
@@ -228,13 +230,15 @@ def test_fp32_ragged_multi_tile_per_step(gpu, orc, bc):
     print("fp32 ragged per-step", bc, "worst abs err (H, Hu, Hv, b):", worst, "outflow m^3:", outflow)
 
 
+@pytest.mark.parametrize("bw", [256, 128])
 @pytest.mark.parametrize("variant", ["inflow", "rain_infiltration", "general_laws"])
-def test_fp32_kernel_variants_per_step(gpu, orc, variant):
+def test_fp32_kernel_variants_per_step(gpu, orc, variant, bw):
     """The FP32 step kernel's other compiled variants, element by element
     against the FP64 oracle one step at a time from the same inputs on the
-    ragged 333 x 271 grid: inflow cells with a hydrograph (the source-term
-    variant), rain and infiltration fields on top, and the general transport
-    laws (A_J from Eq. 4, m = 2.5).  Same per-step FP32 bound as above."""
+    ragged 333 x 271 grid, in 256- and 128-column blocks: inflow cells with a
+    hydrograph (the source-term variant), rain and infiltration fields on
+    top, and the general transport laws (A_J from Eq. 4, m = 2.5).  Same
+    per-step FP32 bound as above."""
     nx, ny = 333, 271
     base = I.ensemble_scenario(max(nx, ny), seed=52, manning=0.035, peak=300.0, d50_scale=1.0)
     H, b = base.H[:ny, :nx].astype(np.float64), base.b[:ny, :nx].astype(np.float64)
@@ -251,7 +255,7 @@ def test_fp32_kernel_variants_per_step(gpu, orc, variant):
         beta = rng.uniform(0.0, 1e-3, (ny, nx))
     if variant == "general_laws":
         kw.update(aj_mode=1, m_exp=2.5)
-    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=256, tile_rows=32, **kw)
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=bw, tile_rows=32, **kw)
     S.set_manning(np.full((ny, nx), 0.035), block=0)
     if src is not None:
         S.set_sources(src, base.hydro_t, base.hydro_Q)
