@@ -251,11 +251,14 @@ swe_status swe_ensemble_member(swe_ensemble *e, int k, swe_handle **member);
  * sized so that the scenarios' steps take about as long; a group runs its
  * scenario's (step, block) items by dataflow: the scenario's next step starts
  * as soon as its own previous step is complete, with no barrier across
- * scenarios.  Every scenario's state must be set.  SWE_ETIMEOUT if a block's
- * wait for a scenario's step gave up (see set_timeout). */
+ * scenarios.  A block whose scenario has no item it could start (its current
+ * step all taken, or all its steps done) runs an open item of another
+ * scenario meanwhile; which block runs an item does not change its result.
+ * Every scenario's state must be set.  SWE_ETIMEOUT if a block's wait for a
+ * scenario's step gave up (see set_timeout). */
 swe_status swe_ensemble_run(swe_ensemble *e, int64_t nsteps);
 
-/* Times each candidate block shape (128 or 256 columns x 16..192 rows) for
+/* Times each candidate block shape (128 or 256 columns x 16..256 rows) for
  * trial_steps steps on the current states, keeps the fastest, and restores
  * the states and times (step counters and inflow totals restart).  Outputs
  * (nullable) the chosen shape. */
