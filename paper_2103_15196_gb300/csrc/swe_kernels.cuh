@@ -1050,18 +1050,18 @@ step_kernel(SweConst c, SweBufs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<T, BW> &S = *reinterpret_cast<StepSmem<T, BW> *>(smem_raw);
     const int count = B.work[0];
-    if (!WALK) {   // dense: at most one entry per CUDA block
+    if constexpr (!WALK) {   // dense: at most one entry per CUDA block
         const int i = blockIdx.x;
         if (i >= count) return;
         const int tile = B.work[2 + i];
         if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
         step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
-        return;
-    }
-    for (int i = blockIdx.x; i < count; i += gridDim.x) {
-        const int tile = B.work[2 + i];
-        if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
-        step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+    } else {
+        for (int i = blockIdx.x; i < count; i += gridDim.x) {
+            const int tile = B.work[2 + i];
+            if (!SWE_IN(tile, c.tiles_x * c.tiles_y)) return;
+            step_tile<T, BW, false, SRC, GEN>(c, B, tile % c.tiles_x, tile / c.tiles_x, S);
+        }
     }
 }
 
