@@ -54,15 +54,20 @@ def _standalone(swe, sc, nsteps, bw, th):
     return out
 
 
-def test_ensemble_matches_standalone_runs(swe):
+@pytest.mark.parametrize("bw", [256, 128])
+def test_ensemble_matches_standalone_runs(swe, bw):
+    """Every member after 120 steps of one persistent launch equals the same
+    scenario run alone, bit for bit, in 256- and 128-thread blocks (the
+    latter six per SM); blocks take items of other scenarios whenever their
+    own scenario's next item would wait, which must not change any result."""
     scs = _scenarios()
-    E = swe.Ensemble([_spec(s) for s in scs], block_cols=256, tile_rows=32)
+    E = swe.Ensemble([_spec(s) for s in scs], block_cols=bw, tile_rows=32)
     for m, sc in zip(E.members, scs):
         _load(m, sc)
     E.run(120)
     for k, (m, sc) in enumerate(zip(E.members, scs)):
         got, t = m.get_state(np.float32), m.t
-        ref, t_ref = _standalone(swe, sc, 120, 256, 32)
+        ref, t_ref = _standalone(swe, sc, 120, bw, 32)
         assert t == t_ref, k
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), k

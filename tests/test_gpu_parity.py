@@ -288,6 +288,50 @@ def test_fp32_kernel_variants_per_step(gpu, orc, variant, bw):
     print("fp32 variant", variant, "worst abs err (H, Hu, Hv, b):", worst)
 
 
+def test_fp32_tall_strips_per_step(gpu, orc):
+    """The benchmark's block shape (128 threads, 120 x 256 cells, six blocks
+    per SM) on a 610 x 530 grid with inflow: 6 column bands (the last 10
+    columns wide) x 3 strips (the last 18 rows high), so most sweep positions
+    run the copy without row-range tests, and the strip ends, the grid's
+    bottom ghost rows and the ragged band all occur.  FP32 state element by
+    element against the FP64 oracle one step at a time from the same inputs,
+    within the per-step FP32 bound of the ragged-grid tests."""
+    nx, ny = 610, 530
+    base = I.ensemble_scenario(max(nx, ny), seed=57, manning=0.035, peak=400.0, d50_scale=1.0)
+    H, b = base.H[:ny, :nx].astype(np.float64), base.b[:ny, :nx].astype(np.float64)
+    Hu, Hv = 0.6 * H, 0.35 * H
+    src = np.ascontiguousarray(base.src[:ny, :nx])
+    assert src.sum() > 0
+    kw = dict(A_J=0.01)
+    S = gpu.Solver(nx, ny, base.dx, precision="fp32", block_cols=128, tile_rows=256, **kw)
+    S.set_manning(np.full((ny, nx), 0.03), block=0)
+    S.set_sources(src, base.hydro_t, base.hydro_Q)
+    S.set_state(H, Hu, Hv, b)
+    assert S.tile == (120, 256)
+    p = orc.Params(nx=nx, ny=ny, dx=base.dx, **kw)
+    ncell = np.full((ny, nx), 0.03)
+    hydro = orc.Hydrograph(base.hydro_t, base.hydro_Q)
+    worst = np.zeros(4)
+    moved = 0.0
+    for it in range(10):
+        t = S.diag()["t"]
+        st = orc.State(*(a.astype(np.float64) for a in S.get_state(np.float32)))
+        o, info = orc.step(p, st, ncell, src=src, hydro=hydro, t=t)
+        outs = [o.arrays()] + [orc.step(pp, st, ncell, src=src, hydro=hydro, t=t)[0].arrays()
+                               for pp in band_params(p)[1:]]
+        dt = S.step()
+        assert dt == pytest.approx(info.dt, rel=1e-5), it
+        got = S.get_state(np.float32)
+        moved = max(moved, np.abs(o.b - st.b).max())
+        for q in range(4):
+            excess, e = band_error(got[q], outs, q)
+            worst[q] = max(worst[q], e.max())
+            assert np.all(excess <= 0), (it, q, e.max(), int((excess > 0).sum()))
+    S.close()
+    assert moved > 1e-7   # the Exner update is exercised
+    print("fp32 tall strips worst abs err (H, Hu, Hv, b):", worst)
+
+
 @pytest.mark.parametrize("shape", [(1, 9), (9, 1), (3, 5), (130, 3)])
 @pytest.mark.parametrize("bc", [(1, 0, 0, 1), (0, 1, 1, 0), (1, 1, 1, 1)], ids=["open_wn", "open_es", "open_all"])
 def test_fp64_parity_tiny_grids_open_boundaries(gpu, orc, shape, bc):
