@@ -118,6 +118,21 @@ def test_fp64_parity_flood_channel_ragged_tiles(gpu, orc):
     print("fp64 flood channel worst rel Linf:", worst)
 
 
+def test_fp64_parity_tall_strips(gpu, orc):
+    """Blocks of the benchmark's height (120 x 256 cells) on a 300 x 560
+    half-wet fractal grid moving across every side: 3 column bands (the last
+    60 columns wide) x 3 strips (the last 48 rows high), so most sweep
+    positions run the copy without row-range tests; per step against the
+    oracle to 1e-11 relative, 40 steps."""
+    nx, ny = 300, 560
+    base = I.half_wet(max(nx, ny), dx=5.0, seed=61, wet_fraction=0.5, dtype=np.float64)
+    H = np.ascontiguousarray(base.H[:ny, :nx])
+    sc = I.Scenario(nx, ny, 5.0, H, 0.4 * H, -0.25 * H, np.ascontiguousarray(base.b[:ny, :nx]),
+                    np.full((1, 1), 0.03), manning_block=1024)
+    worst = _per_step_parity(gpu, orc, sc, 40, bw=128, th=256, A_J=0.01)
+    print("fp64 tall strips worst rel Linf (H, Hu, Hv, b):", worst)
+
+
 @pytest.mark.parametrize("knots", [1, 2, 4, 7])
 def test_fp64_parity_hydrograph_knots(gpu, orc, knots):
     """Inflow hydrographs of 1, 2, 4 (read into registers in one batch) and 7
